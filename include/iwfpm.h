@@ -1,0 +1,135 @@
+/*
+ * iwfpm.h -- C ABI of the GB300 (sm_103a) implementation of the irrational-window-filter
+ * projection method (IWFPM) for quasiperiodic Schroedinger eigenproblems
+ * (Jiang, Li, Ma, Zhang, Zhang, Zhou, arXiv 2404.04507).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an iwf_status. Nothing aborts or exits; after a failure
+ *     iwf_last_error() returns a thread-local message describing it.
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA global memory on
+ *     the plan's device. The caller owns every buffer it passes in; the library owns a plan
+ *     and its workspace and frees them in iwf_plan_destroy.
+ *   - Coefficient vectors hold U~_k for k in the window K_{K,L} in WINDOW ORDER: k_II
+ *     lexicographic (slowest), then k_I lexicographic, each k_I axis running over its 2K_j
+ *     consecutive integers from the slice's lower bound. Element type: complex double
+ *     (interleaved re,im; 16 bytes) for IWF_PREC_F64, complex float (8 bytes) for
+ *     IWF_PREC_C64. A block of nvec vectors is column-major: vector v starts at element v*N.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream). Calls that take a
+ *     stream enqueue their GPU work on it; they return after enqueueing unless stated.
+ */
+#ifndef IWFPM_H
+#define IWFPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IWF_OK = 0,
+  IWF_ERR_ARG = -1,           /* invalid argument (null pointer, size, shape)              */
+  IWF_ERR_SINGULAR_PI = -2,   /* P_I (first d columns of P) singular or cond > 1e12        */
+  IWF_ERR_ALLOC = -3,         /* device or host allocation failed                          */
+  IWF_ERR_CUDA = -4,          /* a CUDA runtime call failed                                */
+  IWF_ERR_NONFINITE = -5,     /* NaN/Inf met in the input or during a solve                */
+  IWF_ERR_BREAKDOWN = -6,     /* Gram matrix not positive definite after re-orthogonalising */
+  IWF_ERR_NOCONV = -7,        /* eigensolver hit maxit; partial results are returned       */
+  IWF_ERR_TIMEOUT = -8,       /* a bounded device wait ran out                             */
+  IWF_ERR_WINDOW_TIE = -9,    /* a window bound lies within 1e-9 of an integer             */
+  IWF_ERR_UNSUPPORTED = -10   /* shape outside what the kernels support (see iwf_plan_create) */
+} iwf_status;
+
+enum { IWF_METHOD_IWFPM = 0, IWF_METHOD_PM = 1 };
+enum { IWF_SHIFT_EXACT = 0, IWF_SHIFT_ROUND = 1 };
+enum { IWF_PREC_F64 = 0, IWF_PREC_C64 = 1 };
+
+typedef struct iwf_plan iwf_plan; /* opaque, library-owned */
+
+typedef struct {
+  int method;      /* IWF_METHOD_IWFPM (irrational window) or IWF_METHOD_PM (box)          */
+  int shift_round; /* IWF_SHIFT_EXACT: lower bound ceil(-K - (Q k_II)_j) as in Sec. 3.2;
+                      IWF_SHIFT_ROUND: -K - round((Q k_II)_j), round half away from zero   */
+  int device;      /* CUDA device ordinal the plan lives on                                */
+} iwf_plan_opts;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int iwf_version(void);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* iwf_last_error(void);
+
+/*
+ * Build a plan for the lifted operator of Sec. 3.1-3.2 and Sec. 4.1.
+ *   d, n   physical and lifted dimension, 1 <= d < n <= 8.
+ *   P      host, d*n doubles, row-major: the projection matrix (Def. 2.1). Its first d
+ *          columns P_I must be invertible (Sec. 3.1); reorder columns otherwise.
+ *   K, L   host, d and n-d ints >= 1: window sizes (vector form, Remark after Fig. 1).
+ *          IWFPM: k_II in [-L,L)^{n-d}, k_I + Q k_II in [-K,K)^d with Q = P_I^{-1} P_II.
+ *          PM: the box [-K,K)^d x [-L,L)^{n-d}.
+ *   opts   host, may be NULL (IWFPM, exact shift, device 0).
+ * Supported: every axis length 2K_j, 2L_j even in [2, 32]; (2K)^d and (2L)^{n-d} at most
+ * 8192 each. The window, its slice bounds and Lambda = 1/2 |P k|^2 (Eq. discrete_Lambda)
+ * are built on the device; the call synchronises the device.
+ * Errors: IWF_ERR_ARG, IWF_ERR_SINGULAR_PI, IWF_ERR_UNSUPPORTED, IWF_ERR_WINDOW_TIE,
+ * IWF_ERR_ALLOC, IWF_ERR_CUDA. On error *plan is set to NULL.
+ */
+iwf_status iwf_plan_create(iwf_plan** plan, int d, int n, const double* P, const int* K,
+                           const int* L, const iwf_plan_opts* opts);
+
+/* Release the plan and all device memory it owns. NULL is ignored. */
+void iwf_plan_destroy(iwf_plan* plan);
+
+/* N = (2K)^d (2L)^{n-d}, the number of window points (DOF, Sec. 3.3). */
+iwf_status iwf_plan_size(const iwf_plan* plan, long long* N);
+
+/* The n grid side lengths (2K_1..2K_d, 2L_1..2L_{n-d}) of K*_{K,L} (Sec. 3.2). */
+iwf_status iwf_plan_lens(const iwf_plan* plan, int* lens);
+
+/*
+ * The window K_{K,L} itself: host output k of N*n ints, row k[i*n + j] = component j of the
+ * true index of window position i (the inverse of the index-shift map, Eqs. inverse1-3).
+ * Synchronises the device.
+ */
+iwf_status iwf_window(const iwf_plan* plan, int* k);
+
+/* Lambda_k = 1/2 |P k|^2 for every window position, host output of N doubles. */
+iwf_status iwf_kinetic(const iwf_plan* plan, double* lam);
+
+/*
+ * Set the lifted potential V(y) = sum_m c_m exp(i m.y) (Sec. 4.1, V sampled on G_{K,L}).
+ *   nmodes >= 0; m host nmodes*n ints (row per mode); re, im host nmodes doubles.
+ * V must be real: every mode m != 0 must come with -m and the conjugate coefficient
+ * (checked to 1e-12 relative; IWF_ERR_ARG otherwise). Modes are folded onto the grid by
+ * the aliasing rule of App. C. When every mode lies on one lifted axis, V is kept as n
+ * per-axis tables; otherwise as a full grid of N values per precision.
+ * Synchronises the device.
+ */
+iwf_status iwf_set_potential(iwf_plan* plan, int nmodes, const int* m, const double* re,
+                             const double* im);
+
+/*
+ * hpsi = H~ psi = Lambda psi + F V F^{-1} psi for nvec vectors (Sec. 4.1, Eq. pseudospectral
+ * vector), with F = T F* (Sec. 3.3, Eq. F): gather through the index shift, inverse n-D
+ * FFT, multiply by V, forward n-D FFT, scatter back to the window and add Lambda psi.
+ *   precision  IWF_PREC_F64 (complex double I/O and arithmetic) or IWF_PREC_C64
+ *              (complex float I/O and arithmetic, Lambda applied in float).
+ *   psi, hpsi  device, N*nvec elements each, column-major, window order; must not overlap.
+ *              Both must be 16-byte aligned.
+ *   nvec >= 0; stream as above. Uses the plan's workspace: calls on one plan must not run
+ *   concurrently on different streams.
+ * Errors: IWF_ERR_ARG (no potential set, bad pointers), IWF_ERR_ALLOC, IWF_ERR_CUDA.
+ */
+iwf_status iwf_apply(iwf_plan* plan, int precision, const void* psi, void* hpsi, int nvec,
+                     void* stream);
+
+/*
+ * Diagonal preconditioner of Eq. precond, M_kk = h_k / (h_k^2 + sum_{m != 0} |Vg_m|^2),
+ * h_k = Lambda_k + Vg_0 + sigma with sigma = sum_{m != 0}|Vg_m| - Vg_0 + 1 (a shift that
+ * makes V + sigma >= 1; it changes no eigenvector). Host outputs: M (N doubles, may be NULL)
+ * and *sigma (may be NULL). Synchronises the device.
+ */
+iwf_status iwf_preconditioner(const iwf_plan* plan, double* M, double* sigma);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IWFPM_H */

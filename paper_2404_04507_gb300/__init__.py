@@ -1,0 +1,126 @@
+"""GB300 (sm_103a) implementation of the IWFPM hot path (arXiv 2404.04507).
+
+``Plan`` wraps the C ABI of ``include/iwfpm.h``: it marshals numpy/torch arguments into the
+library's calls and nothing more. Device buffers are torch CUDA tensors; the CUDA library
+does every step of the computation. Importing ``Plan`` requires the built library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+__all__ = ["Plan"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Plan:
+    """A window plan: P (d x n), K (d), L (n-d), method and shift mode (Sec. 3.1-3.2)."""
+
+    def __init__(self, P, K, L, method: str = "iwfpm", shift_round: bool = False,
+                 device: int = 0):
+        from . import capi
+        self._c = capi
+        P = np.ascontiguousarray(np.asarray(P, dtype=np.float64))
+        d, n = P.shape
+        K = np.ascontiguousarray(np.asarray(K, dtype=np.int32).reshape(d))
+        L = np.ascontiguousarray(np.asarray(L, dtype=np.int32).reshape(n - d))
+        opts = capi.iwf_plan_opts(capi.IWF_METHOD_PM if method == "pm" else capi.IWF_METHOD_IWFPM,
+                                  capi.IWF_SHIFT_ROUND if shift_round else capi.IWF_SHIFT_EXACT,
+                                  int(device))
+        h = C.c_void_p()
+        capi.check(capi.iwf_plan_create(C.byref(h), d, n,
+                                        P.ctypes.data_as(C.POINTER(C.c_double)),
+                                        K.ctypes.data_as(C.POINTER(C.c_int)),
+                                        L.ctypes.data_as(C.POINTER(C.c_int)), C.byref(opts)),
+                   "iwf_plan_create")
+        self.handle = h
+        self.d, self.n, self.device = d, n, int(device)
+        N = C.c_longlong()
+        capi.check(capi.iwf_plan_size(h, C.byref(N)), "iwf_plan_size")
+        self.N = int(N.value)
+        lens = (C.c_int * n)()
+        capi.check(capi.iwf_plan_lens(h, lens), "iwf_plan_lens")
+        self.lens = tuple(int(v) for v in lens)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._c.iwf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def window(self) -> np.ndarray:
+        k = np.empty((self.N, self.n), dtype=np.int32)
+        self._c.check(self._c.iwf_window(self.handle, k.ctypes.data_as(C.POINTER(C.c_int))),
+                      "iwf_window")
+        return k
+
+    def kinetic(self) -> np.ndarray:
+        lam = np.empty(self.N, dtype=np.float64)
+        self._c.check(self._c.iwf_kinetic(self.handle, lam.ctypes.data_as(C.POINTER(C.c_double))),
+                      "iwf_kinetic")
+        return lam
+
+    def set_potential(self, modes, coef):
+        modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, self.n))
+        coef = np.asarray(coef, dtype=np.complex128).reshape(-1)
+        re = np.ascontiguousarray(coef.real)
+        im = np.ascontiguousarray(coef.imag)
+        self._c.check(self._c.iwf_set_potential(self.handle, int(modes.shape[0]),
+                                                modes.ctypes.data_as(C.POINTER(C.c_int)),
+                                                re.ctypes.data_as(C.POINTER(C.c_double)),
+                                                im.ctypes.data_as(C.POINTER(C.c_double))),
+                      "iwf_set_potential")
+
+    def preconditioner(self):
+        M = np.empty(self.N, dtype=np.float64)
+        sigma = C.c_double()
+        self._c.check(self._c.iwf_preconditioner(self.handle,
+                                                 M.ctypes.data_as(C.POINTER(C.c_double)),
+                                                 C.byref(sigma)), "iwf_preconditioner")
+        return M, float(sigma.value)
+
+    @staticmethod
+    def _stream(stream):
+        if stream is None:
+            return C.c_void_p(_torch().cuda.current_stream().cuda_stream)
+        return C.c_void_p(int(stream))
+
+    def _prec(self, t):
+        torch = _torch()
+        if t.dtype == torch.complex128:
+            return self._c.IWF_PREC_F64
+        if t.dtype == torch.complex64:
+            return self._c.IWF_PREC_C64
+        raise TypeError("vectors must be complex128 or complex64 CUDA tensors")
+
+    def _check_block(self, t):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        nvec = 1 if t.dim() == 1 else t.shape[0]
+        if t.numel() != nvec * self.N or not t.is_contiguous():
+            raise ValueError("expected a contiguous (nvec, N) block in window order")
+        return nvec
+
+    def apply(self, psi, out=None, stream=None):
+        """H~ psi for a contiguous (nvec, N) or (N,) complex CUDA tensor (window order)."""
+        nvec = self._check_block(psi)
+        if out is None:
+            out = _torch().empty_like(psi)
+        self._check_block(out)
+        if out.dtype != psi.dtype:
+            raise TypeError("psi and out must share a dtype")
+        self._c.check(self._c.iwf_apply(self.handle, self._prec(psi), C.c_void_p(psi.data_ptr()),
+                                        C.c_void_p(out.data_ptr()), int(nvec),
+                                        self._stream(stream)), "iwf_apply")
+        return out

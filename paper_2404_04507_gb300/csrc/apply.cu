@@ -1,0 +1,384 @@
+// H~ psi = Lambda psi + F V F^{-1} psi on the GPU (Sec. 4.1), with F = T F* (Sec. 3.3).
+//
+// The lifted grid is split into two axis groups: the d k_I axes (innermost in memory, one
+// contiguous slice of (2K)^d points per k_II) and the n-d k_II axes (outermost). One apply is
+// three passes over global memory, each staging tiles in shared memory and running the
+// register DFT codelets of dft.cuh along every axis of its group:
+//   pass A  (k_I group)   window order -> cyclic roll by the slice bound lo_j(k_II) (the
+//                         index shift T^{-1}, Eq. index mod) -> inverse DFT along k_I axes;
+//   pass B  (k_II group)  roll by L_j -> inverse DFT along k_II axes -> multiply by V(y)/N on
+//                         G_{K,L} -> forward DFT along k_II axes -> roll back; in place;
+//   pass C  (k_I group)   forward DFT along k_I axes -> roll back by lo_j (the scatter T) ->
+//                         add Lambda_k psi_k.
+// Rolls are index permutations inside a pencil and cost no arithmetic. Vectors are processed
+// in chunks sized so that the intermediate block stays resident in the 129 MB L2.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "dft.cuh"
+
+namespace iwf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// Shared-memory padding: one spare slot every 32 elements breaks power-of-two strides.
+__device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
+
+// Static description of one axis group inside a tile.
+struct GroupDesc {
+  int ng;                   // axes in the group
+  int len[IWF_MAX_N];       // slowest first
+  int gs[IWF_MAX_N];        // stride of each axis in units of group points (C order)
+  int kI[IWF_MAX_N];        // >= 0: k_I axis index j (roll from the lo table); -1: k_II axis
+  int Lroll[IWF_MAX_N];     // k_II axes: roll offset L_j
+};
+
+struct PassArgs {
+  Geom g;
+  GroupDesc grp;
+  int M;                    // points of the group (product of len)
+  long long inner;          // points of all faster axes
+  int C;                    // inner chunk per tile
+  int Ot;                   // outer indices per tile
+  long long outer;          // number of outer indices
+  long long tiles_inner;    // inner chunks per outer index
+  const void* in;
+  void* out;
+  const void* psi;          // pass C only
+  const void* lam;          // pass C only
+  const int* lo;            // MII x d
+  PotDev pot;               // pass B only
+  long long ld;             // element stride between vectors (= N)
+};
+
+// Roll offset of axis a for outer tile index o: pencil element k* lives at (k* + off) mod len.
+__device__ __forceinline__ int roll_off(const PassArgs& a, int ax, long long o) {
+  const int len = a.grp.len[ax];
+  if (a.grp.kI[ax] >= 0) {
+    const int lo = a.lo[o * a.g.d + a.grp.kI[ax]];
+    int off = (-lo) % len;
+    return off < 0 ? off + len : off;
+  }
+  return a.grp.Lroll[ax] % len;
+}
+
+// One DFT of length LEN along group axis `ax` for every pencil of the tile.
+// ROLL_LOAD: gather with the roll (inverse direction); ROLL_STORE: scatter with it (forward).
+template <typename T, int LEN, int S, bool ROLL_LOAD, bool ROLL_STORE>
+__device__ void axis_dft(typename Vec2<T>::type* tile, const PassArgs& a, int ax, long long o0,
+                         const int* s_off) {
+  using V2 = typename Vec2<T>::type;
+  const int C = a.C, M = a.M;
+  const int gs = a.grp.gs[ax];
+  const int per_o = (M / LEN) * C;
+  const int npen = per_o * a.Ot;
+  for (int p = threadIdx.x; p < npen; p += blockDim.x) {
+    const int ot = p / per_o;
+    const int rem = p - ot * per_o;
+    const int c = rem % C;
+    const int rest = rem / C;
+    const int g0 = (rest / gs) * gs * LEN + rest % gs;
+    const int base = ot * M * C;
+    const int off = (ROLL_LOAD || ROLL_STORE) ? s_off[ot * IWF_MAX_N + ax] : 0;
+    T xr[LEN], xi[LEN];
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) {
+      int src = i;
+      if (ROLL_LOAD) { src = i + off; if (src >= LEN) src -= LEN; }
+      const V2 v = tile[padx(base + (g0 + src * gs) * C + c)];
+      xr[i] = v.x; xi[i] = v.y;
+    }
+    Dft<LEN, S, T>::run(xr, xi);
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) {
+      int dst = i;
+      if (ROLL_STORE) { dst = i + off; if (dst >= LEN) dst -= LEN; }
+      V2 v; v.x = xr[i]; v.y = xi[i];
+      tile[padx(base + (g0 + dst * gs) * C + c)] = v;
+    }
+  }
+}
+
+template <typename T, int S, bool RL, bool RS>
+__device__ void axis_dispatch(typename Vec2<T>::type* tile, const PassArgs& a, int ax, long long o0,
+                              const int* s_off) {
+  switch (a.grp.len[ax]) {
+#define IWF_CASE(L_) case L_: axis_dft<T, L_, S, RL, RS>(tile, a, ax, o0, s_off); break;
+    IWF_CASE(2) IWF_CASE(4) IWF_CASE(6) IWF_CASE(8) IWF_CASE(10) IWF_CASE(12) IWF_CASE(14)
+    IWF_CASE(16) IWF_CASE(18) IWF_CASE(20) IWF_CASE(22) IWF_CASE(24) IWF_CASE(26) IWF_CASE(28)
+    IWF_CASE(30) IWF_CASE(32)
+#undef IWF_CASE
+    default: break;  // lengths are validated on the host
+  }
+}
+
+template <typename T> __device__ __forceinline__ T pot_tab(const PotDev& p, int off);
+template <> __device__ __forceinline__ double pot_tab<double>(const PotDev& p, int off) { return p.tab64[off]; }
+template <> __device__ __forceinline__ float pot_tab<float>(const PotDev& p, int off) { return p.tab32[off]; }
+template <typename T> __device__ __forceinline__ T pot_grid(const PotDev& p, long long i);
+template <> __device__ __forceinline__ double pot_grid<double>(const PotDev& p, long long i) { return p.grid64[i]; }
+template <> __device__ __forceinline__ float pot_grid<float>(const PotDev& p, long long i) { return p.grid32[i]; }
+template <typename T> __device__ __forceinline__ T pot_const(const PotDev& p);
+template <> __device__ __forceinline__ double pot_const<double>(const PotDev& p) { return p.c64; }
+template <> __device__ __forceinline__ float pot_const<float>(const PotDev& p) { return p.c32; }
+
+// KIND 0: pass A, KIND 1: pass B, KIND 2: pass C.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
+  using V2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V2* tile = reinterpret_cast<V2*>(smem_raw);
+  __shared__ int s_off[64 * IWF_MAX_N];
+
+  const long long tile_id = blockIdx.x;
+  const long long o0 = (tile_id / a.tiles_inner) * a.Ot;
+  const long long c0 = (tile_id % a.tiles_inner) * a.C;
+  const int Ot = (int)min((long long)a.Ot, a.outer - o0);
+  const int vec = blockIdx.y;
+  const V2* in = reinterpret_cast<const V2*>(a.in) + (size_t)vec * a.ld;
+  V2* out = reinterpret_cast<V2*>(a.out) + (size_t)vec * a.ld;
+
+  for (int t = threadIdx.x; t < Ot * a.grp.ng; t += blockDim.x) {
+    const int ot = t / a.grp.ng, ax = t % a.grp.ng;
+    s_off[ot * IWF_MAX_N + ax] = roll_off(a, ax, o0 + ot);
+  }
+  // stage the tile: rows of C contiguous elements, one row per (outer, group point)
+  const int C = a.C, M = a.M;
+  const int nel = Ot * M * C;
+  for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+    const int c = e % C;
+    const int gm = e / C;  // ot * M + g
+    const size_t gi = (size_t)(o0 * M + gm) * a.inner + c0 + c;
+    tile[padx(e)] = in[gi];
+  }
+  __syncthreads();
+
+  if (KIND == 0) {
+    for (int ax = 0; ax < a.grp.ng; ++ax) {
+      axis_dispatch<T, +1, true, false>(tile, a, ax, o0, s_off);
+      __syncthreads();
+    }
+  } else if (KIND == 1) {
+    for (int ax = 0; ax < a.grp.ng; ++ax) {
+      axis_dispatch<T, +1, true, false>(tile, a, ax, o0, s_off);
+      __syncthreads();
+    }
+    // multiply by V(y_l)/N: l_II from the group point, l_I from the inner index
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int c = e % C;
+      const int g = (e / C) % M;
+      T v;
+      if (a.pot.kind == 1) {
+        v = pot_const<T>(a.pot);
+        long long rem = c0 + c;              // inner index -> l_I coordinates (C order)
+        for (int j = a.g.d - 1; j >= 0; --j) {
+          const int lj = (int)(rem % a.g.lens[j]);
+          rem /= a.g.lens[j];
+          v += pot_tab<T>(a.pot, a.pot.tab_off[j] + lj);
+        }
+        int gr = g;                          // group point -> l_II coordinates
+        for (int ax = a.grp.ng - 1; ax >= 0; --ax) {
+          const int lj = gr % a.grp.len[ax];
+          gr /= a.grp.len[ax];
+          v += pot_tab<T>(a.pot, a.pot.tab_off[a.g.d + ax] + lj);
+        }
+      } else {
+        v = pot_grid<T>(a.pot, (long long)g * a.inner + c0 + c);
+      }
+      V2 x = tile[padx(e)];
+      x.x *= v; x.y *= v;
+      tile[padx(e)] = x;
+    }
+    __syncthreads();
+    for (int ax = 0; ax < a.grp.ng; ++ax) {
+      axis_dispatch<T, -1, false, true>(tile, a, ax, o0, s_off);
+      __syncthreads();
+    }
+  } else {
+    for (int ax = 0; ax < a.grp.ng; ++ax) {
+      axis_dispatch<T, -1, false, true>(tile, a, ax, o0, s_off);
+      __syncthreads();
+    }
+  }
+
+  if (KIND == 2) {
+    const V2* psi = reinterpret_cast<const V2*>(a.psi) + (size_t)vec * a.ld;
+    const T* lam = reinterpret_cast<const T*>(a.lam);
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int c = e % C;
+      const int gm = e / C;
+      const size_t gi = (size_t)(o0 * M + gm) * a.inner + c0 + c;
+      const V2 x = tile[padx(e)];
+      const V2 p = psi[gi];
+      const T l = lam[gi];
+      V2 r; r.x = x.x + l * p.x; r.y = x.y + l * p.y;
+      out[gi] = r;
+    }
+  } else {
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int c = e % C;
+      const int gm = e / C;
+      const size_t gi = (size_t)(o0 * M + gm) * a.inner + c0 + c;
+      out[gi] = tile[padx(e)];
+    }
+  }
+}
+
+bool g_tw_ready[64] = {};
+
+iwf_status init_twiddles(int device) {
+  if (device >= 0 && device < 64 && g_tw_ready[device]) return IWF_OK;
+  static double2 h64[kTwTotal];
+  static float2 h32[kTwTotal];
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int len = 1; len <= IWF_MAX_LEN; ++len) {
+    for (int j = 0; j < len; ++j) {
+      long double c, s;
+      if (j == 0) { c = 1; s = 0; }
+      else if (2 * j == len) { c = -1; s = 0; }
+      else if (4 * j == len) { c = 0; s = 1; }
+      else if (4 * j == 3 * len) { c = 0; s = -1; }
+      else { const long double t = two_pi * j / len; c = cosl(t); s = sinl(t); }
+      h64[tw_off(len) + j] = make_double2((double)c, (double)s);
+      h32[tw_off(len) + j] = make_float2((float)c, (float)s);
+    }
+  }
+  IWF_CUDA(cudaMemcpyToSymbol(c_tw64, h64, sizeof(h64)));
+  IWF_CUDA(cudaMemcpyToSymbol(c_tw32, h32, sizeof(h32)));
+  if (device >= 0 && device < 64) g_tw_ready[device] = true;
+  return IWF_OK;
+}
+
+template <typename T>
+size_t tile_elems_budget() { return (size_t)(160 * 1024) / sizeof(typename Vec2<T>::type); }
+
+// Choose C (inner chunk) and Ot (outer indices) for a group pass.
+template <typename T>
+void choose_tile(PassArgs& a) {
+  const size_t budget = tile_elems_budget<T>() * 32 / 33;  // room for padding
+  if (a.inner == 1) {
+    a.C = 1;
+    long long ot = (long long)(budget / a.M);
+    ot = ot < 1 ? 1 : ot;
+    // keep several tiles per SM worth of parallelism
+    const long long want = (a.outer + 4 * 152 - 1) / (4 * 152);
+    if (ot > want) ot = want < 1 ? 1 : want;
+    if (ot > 64) ot = 64;
+    a.Ot = (int)ot;
+  } else {
+    a.Ot = 1;
+    long long c = (long long)(budget / a.M);
+    if (c > a.inner) c = a.inner;
+    // largest power of two <= c that divides inner, so chunks tile the inner range exactly
+    long long p = 1;
+    while (p * 2 <= c && a.inner % (p * 2) == 0) p *= 2;
+    a.C = (int)p;
+  }
+  a.tiles_inner = a.inner / a.C;
+}
+
+template <typename T, int KIND>
+iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream) {
+  const size_t elems = (size_t)a.Ot * a.M * a.C;
+  const size_t bytes = (elems + elems / 32 + 1) * sizeof(typename Vec2<T>::type);
+  static bool attr_set[2][3] = {};
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  if (!attr_set[ti][KIND]) {
+    IWF_CUDA(cudaFuncSetAttribute(pass_kernel<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr_set[ti][KIND] = true;
+  }
+  const long long tiles = ((a.outer + a.Ot - 1) / a.Ot) * a.tiles_inner;
+  dim3 grid((unsigned)tiles, (unsigned)nvec);
+  pass_kernel<T, KIND><<<grid, kThreads, bytes, stream>>>(a);
+  IWF_CUDA(cudaGetLastError());
+  return IWF_OK;
+}
+
+template <typename T>
+iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaStream_t stream) {
+  using V2 = typename Vec2<T>::type;
+  const Geom& g = p->g;
+  const int d = g.d, n = g.n;
+  // chunk of vectors whose intermediate block fits comfortably in L2
+  const size_t vbytes = (size_t)g.N * sizeof(V2);
+  int chunk = (int)((size_t)(48u << 20) / vbytes);
+  if (chunk < 1) chunk = 1;
+  if (chunk > nvec) chunk = nvec;
+  if (chunk > 65535) chunk = 65535;
+  IWF_TRY(ensure_workspace(p, vbytes * chunk));
+
+  PotDev pot{};
+  pot.kind = p->pot_kind;
+  for (int j = 0; j < n; ++j) pot.tab_off[j] = p->tab_off[j];
+  pot.tab64 = p->d_tab64; pot.tab32 = p->d_tab32;
+  pot.grid64 = p->d_grid64; pot.grid32 = p->d_grid32;
+  pot.c64 = p->vconst / (double)g.N;
+  pot.c32 = (float)pot.c64;
+
+  PassArgs A{};
+  A.g = g; A.lo = p->d_lo; A.ld = g.N;
+  A.grp.ng = d; A.M = (int)g.MI; A.inner = 1; A.outer = g.MII;
+  for (int j = 0; j < d; ++j) { A.grp.len[j] = g.lens[j]; A.grp.kI[j] = j; A.grp.Lroll[j] = 0; }
+  {
+    int s = 1;
+    for (int j = d - 1; j >= 0; --j) { A.grp.gs[j] = s; s *= g.lens[j]; }
+  }
+  choose_tile<T>(A);
+
+  PassArgs B{};
+  B.g = g; B.lo = p->d_lo; B.ld = g.N; B.pot = pot;
+  B.grp.ng = n - d; B.M = (int)g.MII; B.inner = g.MI; B.outer = 1;
+  for (int j = 0; j < n - d; ++j) {
+    B.grp.len[j] = g.lens[d + j]; B.grp.kI[j] = -1; B.grp.Lroll[j] = g.half[d + j];
+  }
+  {
+    int s = 1;
+    for (int j = n - d - 1; j >= 0; --j) { B.grp.gs[j] = s; s *= g.lens[d + j]; }
+  }
+  choose_tile<T>(B);
+
+  PassArgs Cp = A;
+  Cp.lam = sizeof(T) == 8 ? (const void*)p->d_lam64 : (const void*)p->d_lam32;
+
+  for (int v0 = 0; v0 < nvec; v0 += chunk) {
+    const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+    const V2* in = reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N;
+    V2* out = reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N;
+    V2* work = reinterpret_cast<V2*>(p->d_work);
+    A.in = in; A.out = work;
+    IWF_TRY((launch_pass<T, 0>(A, nv, stream)));
+    B.in = work; B.out = work;
+    IWF_TRY((launch_pass<T, 1>(B, nv, stream)));
+    Cp.in = work; Cp.out = out; Cp.psi = in;
+    IWF_TRY((launch_pass<T, 2>(Cp, nv, stream)));
+  }
+  return IWF_OK;
+}
+
+}  // namespace
+
+iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                      cudaStream_t stream) {
+  if (nvec < 0) return fail(IWF_ERR_ARG, "iwf_apply: nvec < 0");
+  if (nvec == 0) return IWF_OK;
+  if (!psi || !hpsi) return fail(IWF_ERR_ARG, "iwf_apply: null vector pointer");
+  if ((reinterpret_cast<uintptr_t>(psi) | reinterpret_cast<uintptr_t>(hpsi)) & 15)
+    return fail(IWF_ERR_ARG, "iwf_apply: vectors must be 16-byte aligned");
+  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_apply: no potential set");
+  if (nvec > 65535) return fail(IWF_ERR_ARG, "iwf_apply: nvec > 65535");
+  IWF_TRY(init_twiddles(p->device));
+  if (precision == IWF_PREC_F64) return apply_typed<double>(p, psi, hpsi, nvec, stream);
+  if (precision == IWF_PREC_C64) return apply_typed<float>(p, psi, hpsi, nvec, stream);
+  return fail(IWF_ERR_ARG, "iwf_apply: unknown precision");
+}
+
+}  // namespace iwf

@@ -1,0 +1,233 @@
+// C-ABI entry points: plan life cycle, window export, potential, apply, preconditioner.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace iwf {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+iwf_status fail(iwf_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+iwf_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return IWF_ERR_CUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+iwf_status ensure_workspace(iwf_plan* p, size_t bytes) {
+  if (p->work_bytes >= bytes) return IWF_OK;
+  if (p->d_work) { cudaFree(p->d_work); p->d_work = nullptr; p->work_bytes = 0; }
+  cudaError_t e = cudaMalloc(&p->d_work, bytes);
+  if (e != cudaSuccess) { p->d_work = nullptr; return fail(IWF_ERR_ALLOC, "workspace allocation failed"); }
+  p->work_bytes = bytes;
+  return IWF_OK;
+}
+
+namespace {
+
+// Q = P_I^{-1} P_II by LU with partial pivoting (d > 1) or one division per entry (d = 1).
+iwf_status split_q(int d, int n, const double* P, double* Q) {
+  const int m = n - d;
+  if (d == 1) {
+    if (!(std::fabs(P[0]) > 0.0)) return fail(IWF_ERR_SINGULAR_PI, "P_I is zero");
+    for (int i = 0; i < m; ++i) Q[i] = P[1 + i] / P[0];
+    return IWF_OK;
+  }
+  std::vector<double> A(d * d), B(d * m), inv(d * d, 0.0);
+  for (int r = 0; r < d; ++r) {
+    for (int c = 0; c < d; ++c) A[r * d + c] = P[r * n + c];
+    for (int c = 0; c < m; ++c) B[r * m + c] = P[r * n + d + c];
+    inv[r * d + r] = 1.0;
+  }
+  double norm1 = 0.0;
+  for (int c = 0; c < d; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < d; ++r) s += std::fabs(A[r * d + c]);
+    norm1 = std::fmax(norm1, s);
+  }
+  // Gauss-Jordan with partial pivoting on [A | B | I]
+  for (int c = 0; c < d; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < d; ++r)
+      if (std::fabs(A[r * d + c]) > std::fabs(A[piv * d + c])) piv = r;
+    if (!(std::fabs(A[piv * d + c]) > 0.0)) return fail(IWF_ERR_SINGULAR_PI, "P_I is singular");
+    if (piv != c) {
+      for (int k = 0; k < d; ++k) { std::swap(A[c * d + k], A[piv * d + k]); std::swap(inv[c * d + k], inv[piv * d + k]); }
+      for (int k = 0; k < m; ++k) std::swap(B[c * m + k], B[piv * m + k]);
+    }
+    const double pv = A[c * d + c];
+    for (int r = 0; r < d; ++r) {
+      if (r == c) continue;
+      const double f = A[r * d + c] / pv;
+      if (f == 0.0) continue;
+      for (int k = 0; k < d; ++k) { A[r * d + k] -= f * A[c * d + k]; inv[r * d + k] -= f * inv[c * d + k]; }
+      for (int k = 0; k < m; ++k) B[r * m + k] -= f * B[c * m + k];
+    }
+  }
+  double ninv = 0.0;
+  for (int c = 0; c < d; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < d; ++r) s += std::fabs(inv[r * d + c] / A[r * d + r]);
+    ninv = std::fmax(ninv, s);
+  }
+  if (norm1 * ninv > 1e12) return fail(IWF_ERR_SINGULAR_PI, "P_I is ill-conditioned (cond > 1e12)");
+  for (int r = 0; r < d; ++r)
+    for (int k = 0; k < m; ++k) Q[r * m + k] = B[r * m + k] / A[r * d + r];
+  return IWF_OK;
+}
+
+iwf_status plan_create(iwf_plan** out, int d, int n, const double* P, const int* K, const int* L,
+                       const iwf_plan_opts* opts) {
+  if (!out) return fail(IWF_ERR_ARG, "iwf_plan_create: plan pointer is NULL");
+  *out = nullptr;
+  if (!P || !K || !L) return fail(IWF_ERR_ARG, "iwf_plan_create: NULL P, K or L");
+  if (d < 1 || n <= d || n > IWF_MAX_N)
+    return fail(IWF_ERR_ARG, "iwf_plan_create: need 1 <= d < n <= 8");
+  iwf_plan_opts o{IWF_METHOD_IWFPM, IWF_SHIFT_EXACT, 0};
+  if (opts) o = *opts;
+  if (o.method != IWF_METHOD_IWFPM && o.method != IWF_METHOD_PM)
+    return fail(IWF_ERR_ARG, "iwf_plan_create: unknown method");
+  if (o.shift_round != IWF_SHIFT_EXACT && o.shift_round != IWF_SHIFT_ROUND)
+    return fail(IWF_ERR_ARG, "iwf_plan_create: unknown shift mode");
+  for (int i = 0; i < d * n; ++i)
+    if (!std::isfinite(P[i])) return fail(IWF_ERR_NONFINITE, "iwf_plan_create: non-finite P");
+  int ndev = 0;
+  IWF_CUDA(cudaGetDeviceCount(&ndev));
+  if (o.device < 0 || o.device >= ndev) return fail(IWF_ERR_ARG, "iwf_plan_create: bad device");
+
+  Geom g{};
+  g.d = d; g.n = n; g.N = 1; g.MI = 1; g.MII = 1;
+  for (int j = 0; j < n; ++j) {
+    const int h = j < d ? K[j] : L[j - d];
+    if (h < 1) return fail(IWF_ERR_ARG, "iwf_plan_create: K and L must be >= 1");
+    if (2 * h > IWF_MAX_LEN)
+      return fail(IWF_ERR_UNSUPPORTED, "iwf_plan_create: axis length 2K or 2L above 32");
+    g.half[j] = h;
+    g.lens[j] = 2 * h;
+    g.N *= 2 * h;
+    if (j < d) g.MI *= 2 * h; else g.MII *= 2 * h;
+  }
+  if (g.MI > IWF_MAX_GROUP || g.MII > IWF_MAX_GROUP)
+    return fail(IWF_ERR_UNSUPPORTED, "iwf_plan_create: (2K)^d or (2L)^(n-d) above 8192");
+
+  iwf_plan* p = new (std::nothrow) iwf_plan();
+  if (!p) return fail(IWF_ERR_ALLOC, "iwf_plan_create: host allocation failed");
+  p->device = o.device;
+  p->method = o.method;
+  p->shift_round = o.shift_round;
+  p->g = g;
+  std::memcpy(p->P, P, sizeof(double) * d * n);
+  if (o.method == IWF_METHOD_IWFPM) {
+    iwf_status st = split_q(d, n, P, p->Q);
+    if (st != IWF_OK) { delete p; return st; }
+  }
+  DeviceGuard guard(p->device);
+  iwf_status st = IWF_OK;
+  if (cudaMalloc((void**)&p->d_err, sizeof(int)) != cudaSuccess) st = fail(IWF_ERR_ALLOC, "cudaMalloc");
+  if (st == IWF_OK) st = build_window_tables(p);
+  if (st != IWF_OK) { iwf_plan_destroy(p); return st; }
+  *out = p;
+  return IWF_OK;
+}
+
+}  // namespace
+}  // namespace iwf
+
+using namespace iwf;
+
+extern "C" {
+
+int iwf_version(void) { return 100; }
+
+const char* iwf_last_error(void) { return g_last_error.c_str(); }
+
+iwf_status iwf_plan_create(iwf_plan** plan, int d, int n, const double* P, const int* K,
+                           const int* L, const iwf_plan_opts* opts) {
+  clear_error();
+  return plan_create(plan, d, n, P, K, L, opts);
+}
+
+void iwf_plan_destroy(iwf_plan* p) {
+  if (!p) return;
+  DeviceGuard guard(p->device);
+  cudaFree(p->d_lo);
+  cudaFree(p->d_lam64);
+  cudaFree(p->d_lam32);
+  cudaFree(p->d_err);
+  cudaFree(p->d_tab64);
+  cudaFree(p->d_tab32);
+  cudaFree(p->d_grid64);
+  cudaFree(p->d_grid32);
+  cudaFree(p->d_work);
+  delete p;
+}
+
+iwf_status iwf_plan_size(const iwf_plan* p, long long* N) {
+  if (!p || !N) return fail(IWF_ERR_ARG, "iwf_plan_size: NULL argument");
+  *N = p->g.N;
+  return IWF_OK;
+}
+
+iwf_status iwf_plan_lens(const iwf_plan* p, int* lens) {
+  if (!p || !lens) return fail(IWF_ERR_ARG, "iwf_plan_lens: NULL argument");
+  for (int j = 0; j < p->g.n; ++j) lens[j] = p->g.lens[j];
+  return IWF_OK;
+}
+
+iwf_status iwf_window(const iwf_plan* p, int* k) {
+  if (!p || !k) return fail(IWF_ERR_ARG, "iwf_window: NULL argument");
+  DeviceGuard guard(p->device);
+  return export_window(p, k);
+}
+
+iwf_status iwf_kinetic(const iwf_plan* p, double* lam) {
+  if (!p || !lam) return fail(IWF_ERR_ARG, "iwf_kinetic: NULL argument");
+  DeviceGuard guard(p->device);
+  IWF_CUDA(cudaMemcpy(lam, p->d_lam64, sizeof(double) * p->g.N, cudaMemcpyDeviceToHost));
+  return IWF_OK;
+}
+
+iwf_status iwf_set_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
+                             const double* im) {
+  clear_error();
+  if (!p || nmodes < 0 || (nmodes > 0 && (!m || !re || !im)))
+    return fail(IWF_ERR_ARG, "iwf_set_potential: bad arguments");
+  DeviceGuard guard(p->device);
+  return build_potential(p, nmodes, m, re, im);
+}
+
+iwf_status iwf_apply(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                     void* stream) {
+  if (!p) return fail(IWF_ERR_ARG, "iwf_apply: NULL plan");
+  DeviceGuard guard(p->device);
+  return apply_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream);
+}
+
+iwf_status iwf_preconditioner(const iwf_plan* p, double* M, double* sigma) {
+  if (!p) return fail(IWF_ERR_ARG, "iwf_preconditioner: NULL plan");
+  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_preconditioner: no potential set");
+  const double sg = p->voff_abs - p->vg0 + 1.0;
+  if (sigma) *sigma = sg;
+  if (M) {
+    DeviceGuard guard(p->device);
+    std::vector<double> lam(p->g.N);
+    IWF_CUDA(cudaMemcpy(lam.data(), p->d_lam64, sizeof(double) * p->g.N, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < p->g.N; ++i) {
+      const double h = lam[i] + p->vg0 + sg;
+      M[i] = h / (h * h + p->voff_sq);
+    }
+  }
+  return IWF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Shared host/device definitions of the IWFPM library: the plan object, error plumbing and
+// small complex helpers. Every translation unit of the library includes this header.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/iwfpm.h"
+
+#define IWF_MAX_N 8
+#define IWF_MAX_LEN 32       // largest axis length handled by the register DFT codelets
+#define IWF_MAX_GROUP 8192   // largest point count of one axis group staged in shared memory
+
+namespace iwf {
+
+// Records a message for iwf_last_error() and returns the status unchanged.
+iwf_status fail(iwf_status st, const std::string& msg);
+iwf_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define IWF_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::iwf::cuda_fail(e_, #call);           \
+  } while (0)
+
+#define IWF_TRY(call)                                                    \
+  do {                                                                   \
+    iwf_status s_ = (call);                                              \
+    if (s_ != IWF_OK) return s_;                                         \
+  } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Geometry of the lifted grid, passed by value to kernels.
+struct Geom {
+  int d, n;
+  int lens[IWF_MAX_N];     // 2K_1..2K_d, 2L_1..2L_{n-d}
+  int half[IWF_MAX_N];     // K_1..K_d, L_1..L_{n-d}
+  long long N;             // total points
+  long long MI;            // (2K)^d, points of one k_I slice
+  long long MII;           // (2L)^{n-d}, number of slices
+};
+
+// Potential representation on the grid G_{K,L}, already multiplied by 1/N.
+struct PotDev {
+  int kind;                // 1: per-axis tables, 2: full grid
+  int tab_off[IWF_MAX_N];  // offset of axis j's table (length lens[j]) in tab
+  const double* tab64;     // per-axis tables (kind 1)
+  const float* tab32;
+  double c64;              // constant term (kind 1)
+  float c32;
+  const double* grid64;    // kind 2: N values, data layout (l_II slow, l_I fast)
+  const float* grid32;
+};
+
+}  // namespace iwf
+
+struct iwf_plan {
+  int device = 0;
+  int method = IWF_METHOD_IWFPM;
+  int shift_round = IWF_SHIFT_EXACT;
+  iwf::Geom g{};
+  double P[IWF_MAX_N * IWF_MAX_N] = {};
+  double Q[IWF_MAX_N * IWF_MAX_N] = {};   // d x (n-d), row-major; zero for PM
+  int* d_lo = nullptr;                    // MII x d slice lower bounds lo_j(k_II)
+  double* d_lam64 = nullptr;              // N kinetic diagonal
+  float* d_lam32 = nullptr;
+  int* d_err = nullptr;                   // device error word
+  // potential
+  int pot_kind = 0;                       // 0 unset, 1 tables, 2 grid
+  double* d_tab64 = nullptr;
+  float* d_tab32 = nullptr;
+  double* d_grid64 = nullptr;
+  float* d_grid32 = nullptr;
+  double vconst = 0.0;                    // constant term of V (unscaled)
+  double vg0 = 0.0;                       // Re Vg_0
+  double voff_abs = 0.0;                  // sum_{m != 0} |Vg_m|
+  double voff_sq = 0.0;                   // sum_{m != 0} |Vg_m|^2
+  int tab_off[IWF_MAX_N] = {};
+  // workspace for the apply
+  void* d_work = nullptr;
+  size_t work_bytes = 0;
+};
+
+namespace iwf {
+iwf_status ensure_workspace(iwf_plan* p, size_t bytes);
+iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                      cudaStream_t stream);
+iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties
+iwf_status export_window(const iwf_plan* p, int* k_host);
+iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
+                           const double* im);
+}  // namespace iwf

@@ -1,0 +1,333 @@
+// Window construction on the device (Sec. 3.1-3.2) and the lifted potential (Sec. 4.1).
+//
+// For each k_II slice the window holds the k_I with k_I + Q k_II in [-K, K)^d, i.e. the 2K_j
+// consecutive integers from lo_j = ceil(-K_j - q_j), q = Q k_II (exact shift), or
+// lo_j = -K_j - round(q_j) (rounded shift). q is summed left to right with every product
+// and sum rounded separately (__dmul_rn / __dadd_rn, no contraction), so the
+// classification is reproducible. The true index of window position t in a slice is
+// k_j = lo_j + t_j, which is the inverse of the index-shift map rho (Eqs. inverse1-3).
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace iwf {
+
+namespace {
+
+constexpr double kTieEps = 1e-9;
+
+struct WinArgs {
+  Geom g;
+  double Q[IWF_MAX_N * IWF_MAX_N];
+  double P[IWF_MAX_N * IWF_MAX_N];
+  int shift_round;
+};
+
+// k_II of slice s (C order over the k_II positions p_j = k_j + L_j).
+__device__ __forceinline__ void slice_kII(const Geom& g, long long s, int* k) {
+  for (int j = g.n - 1; j >= g.d; --j) {
+    const int len = g.lens[j];
+    k[j] = (int)(s % len) - g.half[j];
+    s /= len;
+  }
+}
+
+__device__ __forceinline__ double round_half_away(double q) {
+  const double r = trunc(q);
+  const double f = __dadd_rn(q, -r);
+  return fabs(f) >= 0.5 ? __dadd_rn(r, copysign(1.0, q)) : r;
+}
+
+__global__ void lo_kernel(WinArgs a, int* lo, int* err) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= a.g.MII) return;
+  int k[IWF_MAX_N];
+  slice_kII(a.g, s, k);
+  const int d = a.g.d, m = a.g.n - d;
+  for (int j = 0; j < d; ++j) {
+    double q = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double prod = __dmul_rn(a.Q[j * m + i], (double)k[d + i]);
+      q = i ? __dadd_rn(q, prod) : prod;
+    }
+    const int K = a.g.half[j];
+    int l;
+    if (a.shift_round) {
+      const double h = q - floor(q) - 0.5;
+      if (fabs(h) < kTieEps && h != 0.0) atomicOr(err, 1);
+      l = -K - (int)round_half_away(q);
+    } else {
+      const double t = __dadd_rn(-(double)K, -q);
+      const double dist = fabs(t - rint(t));
+      if (dist < kTieEps && dist != 0.0) atomicOr(err, 1);
+      l = (int)ceil(t);
+    }
+    lo[s * d + j] = l;
+  }
+}
+
+// True index of window position e (slice-major, k_I C order inside the slice).
+__device__ __forceinline__ void window_index(const Geom& g, const int* lo, long long e, int* k) {
+  const long long s = e / g.MI;
+  long long t = e - s * g.MI;
+  for (int j = g.d - 1; j >= 0; --j) {
+    const int len = g.lens[j];
+    k[j] = lo[s * g.d + j] + (int)(t % len);
+    t /= len;
+  }
+  slice_kII(g, s, k);
+}
+
+__global__ void kinetic_kernel(WinArgs a, const int* lo, double* lam64, float* lam32) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= a.g.N) return;
+  int k[IWF_MAX_N];
+  window_index(a.g, lo, e, k);
+  double s2 = 0.0;
+  for (int r = 0; r < a.g.d; ++r) {
+    double x = 0.0;
+    for (int j = 0; j < a.g.n; ++j) x += a.P[r * a.g.n + j] * (double)k[j];
+    s2 += x * x;
+  }
+  const double lam = 0.5 * s2;
+  lam64[e] = lam;
+  lam32[e] = (float)lam;
+}
+
+__global__ void export_kernel(Geom g, const int* lo, int* kout) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= g.N) return;
+  int k[IWF_MAX_N];
+  window_index(g, lo, e, k);
+  for (int j = 0; j < g.n; ++j) kout[e * g.n + j] = k[j];
+}
+
+// V(y_l) for one grid point from the folded mode list: Re sum_m c_m exp(2 pi i sum_j m_j l_j / len_j).
+struct ModeArgs {
+  Geom g;
+  int nmodes;
+  const int* m;        // nmodes x n, already reduced to [0, len_j)
+  const double* re;
+  const double* im;
+  double scale;        // 1/N
+};
+
+__device__ double mode_sum(const ModeArgs& a, const int* l) {
+  double v = 0.0;
+  for (int q = 0; q < a.nmodes; ++q) {
+    double frac = 0.0;
+    for (int j = 0; j < a.g.n; ++j) {
+      const int len = a.g.lens[j];
+      const int ph = (int)(((long long)a.m[q * a.g.n + j] * l[j]) % len);
+      frac += (double)ph / (double)len;
+    }
+    frac -= floor(frac);
+    double s, c;
+    sincospi(2.0 * frac, &s, &c);
+    v += a.re[q] * c - a.im[q] * s;
+  }
+  return v;
+}
+
+// Per-axis tables: entry (axis j, l) = V restricted to the modes on axis j, at y_j = 2 pi l/len_j.
+__global__ void axis_table_kernel(ModeArgs a, const int* mode_axis, int total, const int* tab_axis,
+                                  const int* tab_l, double* t64, float* t32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int ax = tab_axis[i];
+  int l[IWF_MAX_N] = {0};
+  l[ax] = tab_l[i];
+  double v = 0.0;
+  for (int q = 0; q < a.nmodes; ++q) {
+    if (mode_axis[q] != ax) continue;
+    const int len = a.g.lens[ax];
+    const int ph = (int)(((long long)a.m[q * a.g.n + ax] * l[ax]) % len);
+    double s, c;
+    sincospi(2.0 * (double)ph / (double)len, &s, &c);
+    v += a.re[q] * c - a.im[q] * s;
+  }
+  v *= a.scale;
+  t64[i] = v;
+  t32[i] = (float)v;
+}
+
+// Full grid in data layout: l_II (slow, C order) then l_I (fast, C order).
+__global__ void grid_kernel(ModeArgs a, double* g64, float* g32) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= a.g.N) return;
+  int l[IWF_MAX_N];
+  long long r = e;
+  for (int j = a.g.d - 1; j >= 0; --j) { l[j] = (int)(r % a.g.lens[j]); r /= a.g.lens[j]; }
+  for (int j = a.g.n - 1; j >= a.g.d; --j) { l[j] = (int)(r % a.g.lens[j]); r /= a.g.lens[j]; }
+  const double v = mode_sum(a, l) * a.scale;
+  g64[e] = v;
+  g32[e] = (float)v;
+}
+
+template <typename T>
+iwf_status dev_alloc(T** ptr, size_t count) {
+  if (*ptr) { cudaFree(*ptr); *ptr = nullptr; }
+  if (count == 0) return IWF_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e != cudaSuccess) { *ptr = nullptr; return cuda_fail(e, "cudaMalloc"); }
+  return IWF_OK;
+}
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+iwf_status build_window_tables(iwf_plan* p) {
+  const Geom& g = p->g;
+  WinArgs a{};
+  a.g = g;
+  a.shift_round = p->shift_round;
+  for (int i = 0; i < g.d * (g.n - g.d); ++i) a.Q[i] = p->Q[i];
+  for (int i = 0; i < g.d * g.n; ++i) a.P[i] = p->P[i];
+  IWF_TRY(dev_alloc(&p->d_lo, (size_t)g.MII * g.d));
+  IWF_TRY(dev_alloc(&p->d_lam64, (size_t)g.N));
+  IWF_TRY(dev_alloc(&p->d_lam32, (size_t)g.N));
+  IWF_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+  const int T = 256;
+  lo_kernel<<<(unsigned)((g.MII + T - 1) / T), T>>>(a, p->d_lo, p->d_err);
+  IWF_CUDA(cudaGetLastError());
+  kinetic_kernel<<<(unsigned)((g.N + T - 1) / T), T>>>(a, p->d_lo, p->d_lam64, p->d_lam32);
+  IWF_CUDA(cudaGetLastError());
+  int err = 0;
+  IWF_CUDA(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(IWF_ERR_WINDOW_TIE, "a window bound lies within 1e-9 of an integer");
+  return IWF_OK;
+}
+
+iwf_status export_window(const iwf_plan* p, int* k_host) {
+  const Geom& g = p->g;
+  DevBuf<int> buf;
+  IWF_CUDA(cudaMalloc((void**)&buf.p, (size_t)g.N * g.n * sizeof(int)));
+  const int T = 256;
+  export_kernel<<<(unsigned)((g.N + T - 1) / T), T>>>(g, p->d_lo, buf.p);
+  IWF_CUDA(cudaGetLastError());
+  IWF_CUDA(cudaMemcpy(k_host, buf.p, (size_t)g.N * g.n * sizeof(int), cudaMemcpyDeviceToHost));
+  return IWF_OK;
+}
+
+iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
+                           const double* im) {
+  const Geom& g = p->g;
+  const int n = g.n;
+  // fold every mode onto the grid (aliasing rule) and merge duplicates
+  std::vector<int> fm;
+  std::vector<double> fre, fim;
+  for (int q = 0; q < nmodes; ++q) {
+    if (!std::isfinite(re[q]) || !std::isfinite(im[q]))
+      return fail(IWF_ERR_NONFINITE, "iwf_set_potential: non-finite coefficient");
+    int red[IWF_MAX_N];
+    for (int j = 0; j < n; ++j) {
+      const int len = g.lens[j];
+      int v = m[q * n + j] % len;
+      red[j] = v < 0 ? v + len : v;
+    }
+    int hit = -1;
+    for (size_t r = 0; r < fre.size(); ++r) {
+      bool same = true;
+      for (int j = 0; j < n && same; ++j) same = fm[r * n + j] == red[j];
+      if (same) { hit = (int)r; break; }
+    }
+    if (hit < 0) {
+      fm.insert(fm.end(), red, red + n);
+      fre.push_back(re[q]);
+      fim.push_back(im[q]);
+    } else {
+      fre[hit] += re[q];
+      fim[hit] += im[q];
+    }
+  }
+  // reality check: Vg_{-m} = conj(Vg_m) on the grid
+  double scale = 0.0;
+  for (size_t r = 0; r < fre.size(); ++r) scale = std::fmax(scale, std::hypot(fre[r], fim[r]));
+  for (size_t r = 0; r < fre.size(); ++r) {
+    int neg[IWF_MAX_N];
+    for (int j = 0; j < n; ++j) neg[j] = (g.lens[j] - fm[r * n + j]) % g.lens[j];
+    double cre = 0.0, cim = 0.0;
+    for (size_t s = 0; s < fre.size(); ++s) {
+      bool same = true;
+      for (int j = 0; j < n && same; ++j) same = fm[s * n + j] == neg[j];
+      if (same) { cre = fre[s]; cim = fim[s]; break; }
+    }
+    if (std::fabs(cre - fre[r]) > 1e-12 * scale || std::fabs(cim + fim[r]) > 1e-12 * scale)
+      return fail(IWF_ERR_ARG, "iwf_set_potential: V is not real (modes must come in +-m "
+                               "pairs with conjugate coefficients)");
+  }
+  // preconditioner summaries and the axis classification
+  double vg0 = 0.0, off_abs = 0.0, off_sq = 0.0, vconst = 0.0;
+  std::vector<int> mode_axis(fre.size(), -1);
+  bool separable = true;
+  std::vector<int> um;
+  std::vector<double> ure, uim;
+  for (size_t r = 0; r < fre.size(); ++r) {
+    int nz = 0, ax = -1;
+    for (int j = 0; j < n; ++j) if (fm[r * n + j] != 0) { ++nz; ax = j; }
+    const double a2 = fre[r] * fre[r] + fim[r] * fim[r];
+    if (nz == 0) { vg0 = fre[r]; vconst = fre[r]; continue; }
+    off_abs += std::sqrt(a2);
+    off_sq += a2;
+    if (nz > 1) separable = false;
+    mode_axis[r] = ax;
+  }
+  p->vg0 = vg0; p->voff_abs = off_abs; p->voff_sq = off_sq; p->vconst = vconst;
+
+  DevBuf<int> d_m, d_axis, d_tax, d_tl;
+  DevBuf<double> d_re, d_im;
+  const size_t nm = fre.size();
+  if (nm) {
+    IWF_CUDA(cudaMalloc((void**)&d_m.p, nm * n * sizeof(int)));
+    IWF_CUDA(cudaMalloc((void**)&d_axis.p, nm * sizeof(int)));
+    IWF_CUDA(cudaMalloc((void**)&d_re.p, nm * sizeof(double)));
+    IWF_CUDA(cudaMalloc((void**)&d_im.p, nm * sizeof(double)));
+    IWF_CUDA(cudaMemcpy(d_m.p, fm.data(), nm * n * sizeof(int), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_axis.p, mode_axis.data(), nm * sizeof(int), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_re.p, fre.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_im.p, fim.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  ModeArgs a{};
+  a.g = g; a.nmodes = (int)nm; a.m = d_m.p; a.re = d_re.p; a.im = d_im.p;
+  a.scale = 1.0 / (double)g.N;
+  const int T = 256;
+  IWF_TRY(dev_alloc(&p->d_tab64, 0));
+  IWF_TRY(dev_alloc(&p->d_tab32, 0));
+  IWF_TRY(dev_alloc(&p->d_grid64, 0));
+  IWF_TRY(dev_alloc(&p->d_grid32, 0));
+  if (separable) {
+    std::vector<int> tax, tl;
+    int total = 0;
+    for (int j = 0; j < n; ++j) {
+      p->tab_off[j] = total;
+      for (int l = 0; l < g.lens[j]; ++l) { tax.push_back(j); tl.push_back(l); }
+      total += g.lens[j];
+    }
+    IWF_TRY(dev_alloc(&p->d_tab64, (size_t)total));
+    IWF_TRY(dev_alloc(&p->d_tab32, (size_t)total));
+    IWF_CUDA(cudaMalloc((void**)&d_tax.p, total * sizeof(int)));
+    IWF_CUDA(cudaMalloc((void**)&d_tl.p, total * sizeof(int)));
+    IWF_CUDA(cudaMemcpy(d_tax.p, tax.data(), total * sizeof(int), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_tl.p, tl.data(), total * sizeof(int), cudaMemcpyHostToDevice));
+    axis_table_kernel<<<(total + T - 1) / T, T>>>(a, d_axis.p, total, d_tax.p, d_tl.p,
+                                                  p->d_tab64, p->d_tab32);
+    IWF_CUDA(cudaGetLastError());
+    p->pot_kind = 1;
+  } else {
+    IWF_TRY(dev_alloc(&p->d_grid64, (size_t)g.N));
+    IWF_TRY(dev_alloc(&p->d_grid32, (size_t)g.N));
+    grid_kernel<<<(unsigned)((g.N + T - 1) / T), T>>>(a, p->d_grid64, p->d_grid32);
+    IWF_CUDA(cudaGetLastError());
+    p->pot_kind = 2;
+  }
+  IWF_CUDA(cudaDeviceSynchronize());
+  return IWF_OK;
+}
+
+}  // namespace iwf

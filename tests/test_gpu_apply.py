@@ -1,0 +1,147 @@
+"""GPU parity of the window, the kinetic diagonal and H~ psi against the CPU oracle.
+
+Tolerances: window and slice bounds are integer work and must match bit for bit. The
+FP64 apply is compared element-wise with |err| <= 1e-12 max|H psi|: two FFT passes of
+length <= 2^20 contribute O(log2 N * 2^-53) relative error, far below that bound, while a
+dropped term, sign or index error is O(1). The complex64 apply is held to 2e-5 max|H psi|
+(same argument with 2^-24).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_04507_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 2e-5
+
+
+@pytest.fixture(scope="module")
+def iwf():
+    import paper_2404_04507_gb300 as iwf
+    assert torch.cuda.is_available()
+    return iwf
+
+
+def _plan(iwf, pb, shift_round=False):
+    plan = iwf.Plan(pb.P, pb.K, pb.L, method=pb.method, shift_round=shift_round)
+    plan.set_potential(pb.modes, pb.coef)
+    return plan
+
+
+def _oracle(pb, shift_round=False):
+    win = O.build_window(pb.P, pb.K, pb.L, shift_round=shift_round, method=pb.method)
+    return win, O.grid_coefficients(pb.modes, pb.coef, win.lens)
+
+
+def _gpu_apply(plan, X, dtype):
+    xt = torch.from_numpy(np.ascontiguousarray(X.T)).to(dtype).cuda()
+    y = plan.apply(xt)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.complex128).T
+
+
+def _problems():
+    P3 = np.concatenate([np.eye(3), math.sqrt(2) * np.eye(3)], 1)
+    m3, c3 = W.cosine_modes(6, 3.0)
+    mr, cr = W.random_modes(3, 5, 3, seed=5)
+    return {
+        "qse1d": W.config_1d(),
+        "moire_small": W.config_moire(eps=5.0, K=3, L=4),
+        "moire_ragged": W.config_moire(eps=0.5, K=5, L=3, phases=[0.3, 1.1, 2.0, 4.0]),
+        "pm_moire": W.config_moire(eps=0.5, K=4, L=4, method="pm"),
+        "qse3d_small": W.Problem("qse3d_small", P3, (2, 2, 1), (1, 2, 2), m3, c3),
+        "random_grid_pot": W.Problem("rnd", W.random_P(2, 3, seed=2), (3, 4), (5,), mr, cr),
+        "ex41_round": W.example_41(2.5, 6, 13, shift_round=True),
+        "tiny": W.Problem("tiny", np.array([[1.0, math.sqrt(3.0)]]), (1,), (1,),
+                          *W.cosine_modes(2, 1.0)),
+    }
+
+
+PROBS = _problems()
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_window_bit_exact(iwf, name):
+    pb = PROBS[name]
+    rnd = pb.shift_round
+    plan = _plan(iwf, pb, rnd)
+    win, _ = _oracle(pb, rnd)
+    assert plan.N == win.N
+    assert np.array_equal(plan.window().astype(np.int64), win.k)
+    assert np.allclose(plan.kinetic(), win.lam, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_apply_matches_oracle(iwf, name, prec):
+    pb = PROBS[name]
+    plan = _plan(iwf, pb, pb.shift_round)
+    win, Vg = _oracle(pb, pb.shift_round)
+    X = W.random_block(win.N, 3, seed=11)
+    want = O.apply_stencil(win, Vg, X)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    got = _gpu_apply(plan, X.astype(np.complex64) if prec == "c64" else X, dtype)
+    if prec == "c64":
+        want = O.apply_stencil(win, Vg, X.astype(np.complex64).astype(np.complex128))
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+def test_window_full_size_moire(iwf):
+    pb = W.config_moire(eps=0.5)
+    plan = _plan(iwf, pb)
+    win, _ = _oracle(pb)
+    assert plan.N == 32 ** 4 == win.N
+    assert np.array_equal(plan.window().astype(np.int64), win.k)
+
+
+def test_apply_full_size_moire_block(iwf):
+    # the benchmarked launch: 16 vectors of the 32^4 grid, FP64; the oracle checks 2 of them
+    pb = W.config_moire(eps=5.0)
+    plan = _plan(iwf, pb)
+    win, Vg = _oracle(pb)
+    X = W.random_block(win.N, 16, seed=3)
+    got = _gpu_apply(plan, X, torch.complex128)
+    for c in (0, 15):
+        want = O.apply_stencil(win, Vg, X[:, c])
+        assert np.max(np.abs(got[:, c] - want)) <= TOL64 * np.max(np.abs(want))
+
+
+def test_hermitian_on_gpu(iwf):
+    pb = W.config_moire(eps=0.5, K=6, L=5)
+    plan = _plan(iwf, pb)
+    N = plan.N
+    X = W.random_block(N, 2, seed=9)
+    HX = _gpu_apply(plan, X, torch.complex128)
+    lhs = np.vdot(X[:, 0], HX[:, 1])
+    rhs = np.vdot(HX[:, 0], X[:, 1])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_empty_block_is_noop(iwf):
+    plan = _plan(iwf, PROBS["tiny"])
+    x = torch.zeros((0, plan.N), dtype=torch.complex128, device="cuda")
+    plan.apply(x)
+
+
+def test_errors_are_reported(iwf):
+    from paper_2404_04507_gb300 import capi
+    with pytest.raises(capi.IwfError) as e:
+        iwf.Plan(np.array([[1.0, 0.5 + 1e-12]]), [2], [3])
+    assert e.value.status == -9
+    with pytest.raises(capi.IwfError) as e:
+        iwf.Plan(np.array([[1.0, 2.0 ** 0.5]]), [17], [3])
+    assert e.value.status == -10
+    plan = iwf.Plan(np.array([[1.0, 2.0 ** 0.5]]), [2], [3])
+    x = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    with pytest.raises(capi.IwfError) as e:
+        plan.apply(x)
+    assert e.value.status == -1
+    with pytest.raises(capi.IwfError) as e:
+        plan.set_potential(np.array([[1, 0]]), np.array([1.0 + 0j]))   # not real
+    assert e.value.status == -1
