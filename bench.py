@@ -1,0 +1,358 @@
+"""Benchmark of the IWFPM hot path: H~ psi applies on the 2D moire lifted grid (32^4, FP64).
+
+One step = one H~ psi block apply of 16 vectors on the 32^4 lifted grid (the 2D moire QSE,
+P = [I_2, R_{pi/6}], V = eps sum_j cos y_j, eps = 0.5) through the C ABI, inputs resident
+in HBM. The metric is lifted points per second (points x vectors / time). Prints one JSON
+line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank applies its own independent block (weak scaling, no
+collective on the data path); value = all ranks' points / max-over-ranks time.
+--impl reference times the CPU oracle (the plain FP64 direct-convolution operator) on the
+host cores with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2404_04507_gb300 import workloads as W  # noqa: E402
+
+METRIC = "H·ψ applies/s (lifted pts/s) & time to k eigenpairs @1e-10 resid, IWFPM vs PM"
+UNIT = "lifted pts/s"
+NVEC = 16
+EPS = 0.5
+# FP64 peak of a GB300 from its unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# = 1.26e12, i.e. the nominal 1.25 TFLOP/s. The FP64 passes are bound by it, not by HBM.
+FP64_PEAK_TFLOPS = 1.25
+PROFILE_FILE = os.path.join(ROOT, "profiles", "apply_pass_b_moire32_f64.txt")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fft_flops_per_point(lens) -> float:
+    """Algorithmic flops per point and vector of one apply: 2 FFTs at 5 log2 N, V, Lambda."""
+    return 10.0 * math.log2(float(np.prod(lens))) + 6.0
+
+
+def pass_b_flops_per_point(lens, d) -> float:
+    """Pass B: inverse + forward DFT along the k_II axes (5 log2 M_II each) and V (2 flops)."""
+    mii = float(np.prod(lens[d:]))
+    return 10.0 * math.log2(mii) + 2.0
+
+
+def _source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_2404_04507_gb300/csrc/apply.cu", "paper_2404_04507_gb300/csrc/dft.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per pass-B launch from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        kv = {}
+        with open(PROFILE_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_hash") != _source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_scaled"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_oracle_rate(pb, budget_s: float = 12.0, max_vectors: int = 64):
+    """Oracle apply (numpy direct convolution, one thread) on vectors of the same workload."""
+    import oracle as O
+    win = O.build_window(pb.P, pb.K, pb.L)
+    Vg = O.grid_coefficients(pb.modes, pb.coef, win.lens)
+    X = W.random_block(win.N, 1, seed=123)[:, 0]
+    done, t0 = 0, time.perf_counter()
+    while done < max_vectors:
+        O.apply_stencil(win, Vg, X)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done * win.N / dt, done, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    pb = W.config_moire(eps=EPS)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(pb, budget_s=0.0, max_vectors=1)
+    vals, per = [], []
+    for _ in range(args.steps):
+        v, nv, dt = cpu_oracle_rate(pb, budget_s=0.0, max_vectors=1)
+        vals.append(v)
+        per.append(dt)
+    value = float(np.median(vals))
+    sample = f"1 vector of the 32^4 grid per step ({pb.dof} points), numpy, 1 thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(per)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "moire2d_32^4_f64_apply", "grid": [32, 32, 32, 32],
+                   "nvec_per_step": 1, "eps": EPS, "theta": "pi/6", "method": "iwfpm"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for --impl ours")
+    torch.cuda.set_device(local)
+    import paper_2404_04507_gb300 as iwf
+
+    pb = W.config_moire(eps=EPS)
+    plan = iwf.Plan(pb.P, pb.K, pb.L, device=local)
+    plan.set_potential(pb.modes, pb.coef)
+    N = plan.N
+    X = W.random_block(N, NVEC, seed=1000 + rank)
+    x = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        plan.apply(x, y)
+    torch.cuda.synchronize()
+
+    # timed region: K block applies, inputs (268 MB) larger than L2, device events
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = iwf.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.apply(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = iwf.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    pts = float(N) * NVEC
+    value = pts * ws / (ms * 1e-3)
+
+    # dominant kernel (pass B) per-launch duration, events on the launching stream
+    pass_ms, pass_n = np.zeros(3), np.zeros(3)
+    nprof = max(3, args.steps // 2)
+    for _ in range(nprof):
+        ms3, n3 = plan.apply_profile(x, y)
+        pass_ms += ms3
+        pass_n += n3
+    per_launch = pass_ms / np.maximum(pass_n, 1)
+    chunk = NVEC * nprof / pass_n[1]          # vectors processed by one pass-B launch
+    flops_b = pass_b_flops_per_point(plan.lens, plan.d) * N * chunk
+    achieved = flops_b / (per_launch[1] * 1e-3) / 1e12
+    traffic = _ncu_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic,
+                "kernel": "pass_kernel<double,1> (k_II inverse DFT, x V, k_II forward DFT)",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25)",
+                "vectors_per_launch": chunk, "launch_ms": per_launch[1],
+                "pass_ms_share": (pass_ms / pass_ms.sum()).round(4).tolist()}
+
+    # complex64 apply of the same block (the mixed-precision path), HBM-bound
+    xc = x.to(torch.complex64)
+    yc = torch.empty_like(xc)
+    for _ in range(3):
+        plan.apply(xc, yc)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nrep = max(args.steps, 10)
+    for _ in range(nrep):
+        plan.apply(xc, yc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_c64 = e0.elapsed_time(e1) / nrep
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    gbs = 16.0 * pts / (ms_c64 * 1e-3) / 1e9
+    c64 = {"value": pts / (ms_c64 * 1e-3), "unit": UNIT, "ms_per_step": ms_c64,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": gbs / hbm, "traffic": None,
+                        "algorithmic_bytes": "16 B per point and vector (read psi, write H psi)"}}
+
+    # end to end through the C ABI from pinned host memory
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        x.copy_(xh, non_blocking=True)
+        plan.apply(x, y)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        plan.apply(x, y)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    nbytes = x.numel() * x.element_size()
+    e2e = {"value": pts * ws / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, nv, dt = cpu_oracle_rate(pb)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nv} vector(s) of the 32^4 grid in {dt:.1f} s, numpy direct "
+                         f"convolution, 1 thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "moire2d_32^4_f64_block16_apply", "grid": list(plan.lens),
+                   "nvec": NVEC, "eps": EPS, "theta": "pi/6", "method": "iwfpm",
+                   "parallelism": f"replicas{ws}",
+                   "l2": "inputs 268 MB > 129 MB L2; no flush needed"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk, "c64_apply": c64,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

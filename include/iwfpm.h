@@ -129,6 +129,19 @@ iwf_status iwf_apply(iwf_plan* plan, int precision, const void* psi, void* hpsi,
  */
 iwf_status iwf_preconditioner(const iwf_plan* plan, double* M, double* sigma);
 
+/*
+ * Same computation as iwf_apply, with CUDA events recorded on `stream` around every pass
+ * kernel (pass A: inverse DFT along k_I with the gather; pass B: k_II inverse DFT, V,
+ * k_II forward DFT; pass C: forward DFT along k_I with the scatter and Lambda psi).
+ * Synchronises the stream. Host outputs (may be NULL): pass_ms[3] = summed device time of
+ * each pass in this call (ms), launches[3] = number of kernel launches of each pass.
+ */
+iwf_status iwf_apply_profile(iwf_plan* plan, int precision, const void* psi, void* hpsi,
+                             int nvec, void* stream, double* pass_ms, int* launches);
+
+/* Number of kernels this library has launched in this process (all devices, all plans). */
+long long iwf_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

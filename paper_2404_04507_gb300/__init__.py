@@ -124,3 +124,22 @@ class Plan:
                                         C.c_void_p(out.data_ptr()), int(nvec),
                                         self._stream(stream)), "iwf_apply")
         return out
+
+    def apply_profile(self, psi, out, stream=None):
+        """iwf_apply_profile: same result as apply(); returns (pass_ms[3], launches[3])."""
+        nvec = self._check_block(psi)
+        self._check_block(out)
+        ms = (C.c_double * 3)()
+        nl = (C.c_int * 3)()
+        self._c.check(self._c.iwf_apply_profile(self.handle, self._prec(psi),
+                                                C.c_void_p(psi.data_ptr()),
+                                                C.c_void_p(out.data_ptr()), int(nvec),
+                                                self._stream(stream), ms, nl),
+                      "iwf_apply_profile")
+        return [float(v) for v in ms], [int(v) for v in nl]
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the CUDA library so far in this process."""
+    from . import capi
+    return int(capi.iwf_kernel_launches())

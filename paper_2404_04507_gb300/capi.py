@@ -54,6 +54,9 @@ _PROTOS = {
                                C.POINTER(C.c_double)]),
     "iwf_apply": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_preconditioner": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "iwf_apply_profile": (_i, [_vp, _i, _vp, _vp, _i, _vp, C.POINTER(C.c_double),
+                               C.POINTER(_i)]),
+    "iwf_kernel_launches": (_ll, []),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _fn = getattr(lib, _name)

@@ -12,6 +12,7 @@
 //                         add Lambda_k psi_k.
 // Rolls are index permutations inside a pencil and cost no arithmetic. Vectors are processed
 // in chunks sized so that the intermediate block stays resident in the 129 MB L2.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -286,7 +287,7 @@ void choose_tile(PassArgs& a) {
 }
 
 template <typename T, int KIND>
-iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream) {
+iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer) {
   const size_t elems = (size_t)a.Ot * a.M * a.C;
   const size_t bytes = (elems + elems / 32 + 1) * sizeof(typename Vec2<T>::type);
   static bool attr_set[2][3] = {};
@@ -298,13 +299,24 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream) {
   }
   const long long tiles = ((a.outer + a.Ot - 1) / a.Ot) * a.tiles_inner;
   dim3 grid((unsigned)tiles, (unsigned)nvec);
+  if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
   pass_kernel<T, KIND><<<grid, kThreads, bytes, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
+  count_launch();
+  if (timer) {
+    IWF_CUDA(cudaEventRecord(timer->ev[1], stream));
+    IWF_CUDA(cudaEventSynchronize(timer->ev[1]));
+    float ms = 0.f;
+    IWF_CUDA(cudaEventElapsedTime(&ms, timer->ev[0], timer->ev[1]));
+    timer->ms[KIND] += ms;
+    timer->launches[KIND] += 1;
+  }
   return IWF_OK;
 }
 
 template <typename T>
-iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaStream_t stream) {
+iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaStream_t stream,
+                       PassTimer* timer) {
   using V2 = typename Vec2<T>::type;
   const Geom& g = p->g;
   const int d = g.d, n = g.n;
@@ -355,19 +367,25 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     V2* out = reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N;
     V2* work = reinterpret_cast<V2*>(p->d_work);
     A.in = in; A.out = work;
-    IWF_TRY((launch_pass<T, 0>(A, nv, stream)));
+    IWF_TRY((launch_pass<T, 0>(A, nv, stream, timer)));
     B.in = work; B.out = work;
-    IWF_TRY((launch_pass<T, 1>(B, nv, stream)));
+    IWF_TRY((launch_pass<T, 1>(B, nv, stream, timer)));
     Cp.in = work; Cp.out = out; Cp.psi = in;
-    IWF_TRY((launch_pass<T, 2>(Cp, nv, stream)));
+    IWF_TRY((launch_pass<T, 2>(Cp, nv, stream, timer)));
   }
   return IWF_OK;
 }
 
 }  // namespace
 
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, PassTimer* timer) {
   if (nvec < 0) return fail(IWF_ERR_ARG, "iwf_apply: nvec < 0");
   if (nvec == 0) return IWF_OK;
   if (!psi || !hpsi) return fail(IWF_ERR_ARG, "iwf_apply: null vector pointer");
@@ -376,8 +394,8 @@ iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, i
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_apply: no potential set");
   if (nvec > 65535) return fail(IWF_ERR_ARG, "iwf_apply: nvec > 65535");
   IWF_TRY(init_twiddles(p->device));
-  if (precision == IWF_PREC_F64) return apply_typed<double>(p, psi, hpsi, nvec, stream);
-  if (precision == IWF_PREC_C64) return apply_typed<float>(p, psi, hpsi, nvec, stream);
+  if (precision == IWF_PREC_F64) return apply_typed<double>(p, psi, hpsi, nvec, stream, timer);
+  if (precision == IWF_PREC_C64) return apply_typed<float>(p, psi, hpsi, nvec, stream, timer);
   return fail(IWF_ERR_ARG, "iwf_apply: unknown precision");
 }
 

@@ -213,6 +213,29 @@ iwf_status iwf_apply(iwf_plan* p, int precision, const void* psi, void* hpsi, in
   return apply_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream);
 }
 
+iwf_status iwf_apply_profile(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                             void* stream, double* pass_ms, int* launches) {
+  if (!p) return fail(IWF_ERR_ARG, "iwf_apply_profile: NULL plan");
+  DeviceGuard guard(p->device);
+  PassTimer t;
+  IWF_CUDA(cudaEventCreate(&t.ev[0]));
+  if (cudaEventCreate(&t.ev[1]) != cudaSuccess) {
+    cudaEventDestroy(t.ev[0]);
+    return fail(IWF_ERR_CUDA, "cudaEventCreate");
+  }
+  iwf_status st = apply_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream, &t);
+  cudaEventDestroy(t.ev[0]);
+  cudaEventDestroy(t.ev[1]);
+  if (st != IWF_OK) return st;
+  for (int i = 0; i < 3; ++i) {
+    if (pass_ms) pass_ms[i] = t.ms[i];
+    if (launches) launches[i] = t.launches[i];
+  }
+  return IWF_OK;
+}
+
+long long iwf_kernel_launches(void) { return launch_count(); }
+
 iwf_status iwf_preconditioner(const iwf_plan* p, double* M, double* sigma) {
   if (!p) return fail(IWF_ERR_ARG, "iwf_preconditioner: NULL plan");
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_preconditioner: no potential set");

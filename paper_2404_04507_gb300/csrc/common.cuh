@@ -99,8 +99,16 @@ struct iwf_plan {
 
 namespace iwf {
 iwf_status ensure_workspace(iwf_plan* p, size_t bytes);
+// Optional per-pass timing of one apply (events on the launching stream).
+struct PassTimer {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double ms[3] = {0, 0, 0};
+  int launches[3] = {0, 0, 0};
+};
 iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
-                      cudaStream_t stream);
+                      cudaStream_t stream, PassTimer* timer = nullptr);
+void count_launch();
+long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties
 iwf_status export_window(const iwf_plan* p, int* k_host);
 iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
