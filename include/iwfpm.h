@@ -142,6 +142,30 @@ iwf_status iwf_apply_profile(iwf_plan* plan, int precision, const void* psi, voi
 /* Number of kernels this library has launched in this process (all devices, all plans). */
 long long iwf_kernel_launches(void);
 
+/*
+ * iwf_apply without any device allocation. The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory while they run -- for example a
+ * program whose device memory belongs to a pool or framework allocator that forbids direct
+ * cudaMalloc/cudaFree, or a latency-critical loop where the implicit device
+ * synchronisation of cudaMalloc/cudaFree would stall other work. iwf_apply may grow the
+ * plan's workspace on a call with a larger block; this call never does.
+ *   Same arguments, layout and result as iwf_apply.
+ *   Scratch: the block between the passes lives in a fixed 32 MiB array compiled into the
+ *   library (every GPU that loads the library holds it until the process exits). One
+ *   vector must fit: N * 16 bytes (IWF_PREC_F64) or N * 8 bytes (IWF_PREC_C64) at most
+ *   33554432; larger plans return IWF_ERR_UNSUPPORTED with the sizes in the message.
+ *   Blocks are processed a chunk of vectors at a time; nothing in the array needs to start
+ *   at zero, and each call overwrites what the previous one left there.
+ *   The first call on a device looks up the array's device address (no allocation); make
+ *   that first call before starting any stream capture on that device.
+ *   All calls share the one array: calls whose GPU work overlaps (different streams, or
+ *   different host threads, without ordering between them) race and give wrong results.
+ *   Order them on one stream or with events.
+ * Errors: as iwf_apply, plus IWF_ERR_UNSUPPORTED for a plan too large for the array.
+ */
+iwf_status iwf_apply_noalloc(iwf_plan* plan, int precision, const void* psi, void* hpsi,
+                             int nvec, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,7 @@ _PROTOS = {
     "iwf_apply_profile": (_i, [_vp, _i, _vp, _vp, _i, _vp, C.POINTER(C.c_double),
                                C.POINTER(_i)]),
     "iwf_kernel_launches": (_ll, []),
+    "iwf_apply_noalloc": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _fn = getattr(lib, _name)

@@ -13,6 +13,8 @@
 // Rolls are index permutations inside a pencil and cost no arithmetic. Vectors are processed
 // in chunks sized so that the intermediate block stays resident in the 129 MB L2.
 #include <atomic>
+#include <mutex>
+#include <string>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -316,7 +318,7 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
 
 template <typename T>
 iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaStream_t stream,
-                       PassTimer* timer) {
+                       PassTimer* timer, void* ext_work = nullptr, size_t ext_bytes = 0) {
   using V2 = typename Vec2<T>::type;
   const Geom& g = p->g;
   const int d = g.d, n = g.n;
@@ -326,7 +328,15 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
   if (chunk < 1) chunk = 1;
   if (chunk > nvec) chunk = nvec;
   if (chunk > 65535) chunk = 65535;
-  IWF_TRY(ensure_workspace(p, vbytes * chunk));
+  void* work = ext_work;
+  if (ext_work) {
+    const int fit = (int)(ext_bytes / vbytes);
+    if (fit < 1) return fail(IWF_ERR_UNSUPPORTED, "caller workspace smaller than one vector");
+    if (chunk > fit) chunk = fit;
+  } else {
+    IWF_TRY(ensure_workspace(p, vbytes * chunk));
+    work = p->d_work;
+  }
 
   PotDev pot{};
   pot.kind = p->pot_kind;
@@ -365,12 +375,12 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
     const V2* in = reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N;
     V2* out = reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N;
-    V2* work = reinterpret_cast<V2*>(p->d_work);
-    A.in = in; A.out = work;
+    V2* wk = reinterpret_cast<V2*>(work);
+    A.in = in; A.out = wk;
     IWF_TRY((launch_pass<T, 0>(A, nv, stream, timer)));
-    B.in = work; B.out = work;
+    B.in = wk; B.out = wk;
     IWF_TRY((launch_pass<T, 1>(B, nv, stream, timer)));
-    Cp.in = work; Cp.out = out; Cp.psi = in;
+    Cp.in = wk; Cp.out = out; Cp.psi = in;
     IWF_TRY((launch_pass<T, 2>(Cp, nv, stream, timer)));
   }
   return IWF_OK;
@@ -397,6 +407,59 @@ iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, i
   if (precision == IWF_PREC_F64) return apply_typed<double>(p, psi, hpsi, nvec, stream, timer);
   if (precision == IWF_PREC_C64) return apply_typed<float>(p, psi, hpsi, nvec, stream, timer);
   return fail(IWF_ERR_ARG, "iwf_apply: unknown precision");
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free apply. The intermediate block lives in a fixed array compiled into this
+// library instead of the plan's workspace, so the call never allocates device memory.
+// The array is created on every GPU that loads the library and stays until the process
+// exits. Its device address is looked up once per device, on that device's first call.
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {};
+}  // namespace
+
+// Device address of the fixed array on the current device (the caller makes it current).
+static iwf_status static_scratch_address(int device, void** out) {
+  if (device < 0 || device >= 64) return fail(IWF_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* addr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_scratch_addr[device] = addr;
+  }
+  *out = g_scratch_addr[device];
+  return IWF_OK;
+}
+
+iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                              cudaStream_t stream) {
+  if (nvec < 0) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: nvec < 0");
+  if (nvec == 0) return IWF_OK;
+  if (!psi || !hpsi) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: null vector pointer");
+  if ((reinterpret_cast<uintptr_t>(psi) | reinterpret_cast<uintptr_t>(hpsi)) & 15)
+    return fail(IWF_ERR_ARG, "iwf_apply_noalloc: vectors must be 16-byte aligned");
+  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: no potential set");
+  if (nvec > 65535) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: nvec > 65535");
+  if (precision != IWF_PREC_F64 && precision != IWF_PREC_C64)
+    return fail(IWF_ERR_ARG, "iwf_apply_noalloc: unknown precision");
+  const size_t elt = precision == IWF_PREC_F64 ? 16 : 8;
+  const size_t need = (size_t)p->g.N * elt;
+  if (need > kStaticScratchBytes)
+    return fail(IWF_ERR_UNSUPPORTED,
+                "iwf_apply_noalloc: one vector needs " + std::to_string(need) +
+                    " bytes of scratch, above the fixed maximum of " +
+                    std::to_string(kStaticScratchBytes) + " bytes");
+  void* scratch = nullptr;
+  IWF_TRY(static_scratch_address(p->device, &scratch));
+  IWF_TRY(init_twiddles(p->device));
+  if (precision == IWF_PREC_F64)
+    return apply_typed<double>(p, psi, hpsi, nvec, stream, nullptr, scratch, kStaticScratchBytes);
+  return apply_typed<float>(p, psi, hpsi, nvec, stream, nullptr, scratch, kStaticScratchBytes);
 }
 
 }  // namespace iwf

@@ -236,6 +236,13 @@ iwf_status iwf_apply_profile(iwf_plan* p, int precision, const void* psi, void* 
 
 long long iwf_kernel_launches(void) { return launch_count(); }
 
+iwf_status iwf_apply_noalloc(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                             void* stream) {
+  if (!p) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: NULL plan");
+  DeviceGuard guard(p->device);
+  return apply_noalloc_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream);
+}
+
 iwf_status iwf_preconditioner(const iwf_plan* p, double* M, double* sigma) {
   if (!p) return fail(IWF_ERR_ARG, "iwf_preconditioner: NULL plan");
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_preconditioner: no potential set");

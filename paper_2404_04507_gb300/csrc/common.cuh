@@ -107,6 +107,8 @@ struct PassTimer {
 };
 iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                       cudaStream_t stream, PassTimer* timer = nullptr);
+iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                              cudaStream_t stream);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties
