@@ -129,6 +129,48 @@ iwf_status iwf_apply(iwf_plan* plan, int precision, const void* psi, void* hpsi,
  */
 iwf_status iwf_preconditioner(const iwf_plan* plan, double* M, double* sigma);
 
+typedef struct {
+  int nev;          /* eigenpairs wanted, 1 <= nev <= block                                 */
+  int block;        /* LOBPCG block size b (0: b = nev), at most 16                          */
+  int maxit;        /* iteration limit over both phases (0: 1000)                            */
+  double tol;       /* stop when |H~x_i - lambda_i x_i|_2 <= tol for i < nev, |x_i|_2 = 1
+                       (0: 1e-10)                                                           */
+  int precision;    /* IWF_PREC_F64: every phase in complex double. IWF_PREC_C64: a first
+                       phase with complex-float blocks and apply (FP64 small problems) until
+                       the residuals reach c64_tol or stall, then complex double to tol    */
+  double c64_tol;   /* residual target of the complex-float phase (0: 1e-4)                  */
+  unsigned long long seed; /* seed of the start block when X0 is NULL                       */
+} iwf_solve_opts;
+
+typedef struct {
+  int iters;        /* LOBPCG iterations, both phases                                       */
+  int iters_c64;    /* of which in the complex-float phase                                  */
+  long long applies;/* vectors passed through H~                                            */
+  int converged;    /* 1 when every wanted residual reached tol                             */
+  double max_resid; /* largest final residual among the nev wanted pairs                    */
+  double seconds;   /* wall time of the call                                                */
+} iwf_solve_info;
+
+/*
+ * Lowest nev eigenpairs of H~ (Sec. 4.1) by block LOBPCG (Alg. 2 in block form, Knyazev's
+ * method cited there) with the diagonal preconditioner of Eq. precond, shifted as described
+ * for iwf_preconditioner. Every step runs on the device: the FFT apply, the residual and
+ * preconditioner, Gram products, orthonormalisation and the small Rayleigh-Ritz eigenproblem
+ * (one-CTA Jacobi in FP64); the host reads only the residual norms once per iteration.
+ *   X0     device, N*block complex doubles (window order, column-major) or NULL for a seeded
+ *          random start (splitmix64 counter generator).
+ *   evals  host, nev doubles, ascending.   resid host, nev doubles (may be NULL).
+ *   evecs  device, N*nev complex doubles, orthonormal, column-major, window order.
+ *   info   host (may be NULL).
+ * The call allocates its workspace (about 11 blocks of N*block complex values) and
+ * synchronises `stream` before returning.
+ * Errors: IWF_ERR_ARG, IWF_ERR_ALLOC, IWF_ERR_CUDA, IWF_ERR_NONFINITE, IWF_ERR_BREAKDOWN,
+ * IWF_ERR_NOCONV (outputs then hold the last iterate).
+ */
+iwf_status iwf_eigensolve(iwf_plan* plan, const iwf_solve_opts* opts, const void* X0,
+                          double* evals, void* evecs, double* resid, iwf_solve_info* info,
+                          void* stream);
+
 /*
  * Same computation as iwf_apply, with CUDA events recorded on `stream` around every pass
  * kernel (pass A: inverse DFT along k_I with the gather; pass B: k_II inverse DFT, V,

@@ -139,6 +139,30 @@ class Plan:
         return [float(v) for v in ms], [int(v) for v in nl]
 
 
+    def eigensolve(self, nev, block=0, tol=1e-10, maxit=0, precision="f64", c64_tol=0.0,
+                   seed=1, X0=None, stream=None, raise_noconv=True):
+        """Lowest nev eigenpairs (iwf_eigensolve). Returns (evals, evecs (nev, N), resid, info)."""
+        torch = _torch()
+        c = self._c
+        opts = c.iwf_solve_opts(int(nev), int(block), int(maxit), float(tol),
+                                c.IWF_PREC_F64 if precision == "f64" else c.IWF_PREC_C64,
+                                float(c64_tol), int(seed))
+        evals = np.zeros(nev)
+        resid = np.zeros(nev)
+        evecs = torch.empty((nev, self.N), dtype=torch.complex128, device=f"cuda:{self.device}")
+        info = c.iwf_solve_info()
+        x0 = C.c_void_p(X0.data_ptr()) if X0 is not None else None
+        st = c.iwf_eigensolve(self.handle, C.byref(opts), x0,
+                              evals.ctypes.data_as(C.POINTER(C.c_double)),
+                              C.c_void_p(evecs.data_ptr()),
+                              resid.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info),
+                              self._stream(stream))
+        if st != 0 and not (st == -7 and not raise_noconv):
+            c.check(st, "iwf_eigensolve")
+        out = {f: getattr(info, f) for f, _ in c.iwf_solve_info._fields_}
+        return evals, evecs, resid, out
+
+
 def kernel_launches() -> int:
     """Kernels launched by the CUDA library so far in this process."""
     from . import capi

@@ -31,6 +31,16 @@ class iwf_plan_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("shift_round", C.c_int), ("device", C.c_int)]
 
 
+class iwf_solve_opts(C.Structure):
+    _fields_ = [("nev", C.c_int), ("block", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
+                ("precision", C.c_int), ("c64_tol", C.c_double), ("seed", C.c_ulonglong)]
+
+
+class iwf_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("iters_c64", C.c_int), ("applies", C.c_longlong),
+                ("converged", C.c_int), ("max_resid", C.c_double), ("seconds", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run python -m paper_2404_04507_gb300.build")
@@ -58,6 +68,8 @@ _PROTOS = {
                                C.POINTER(_i)]),
     "iwf_kernel_launches": (_ll, []),
     "iwf_apply_noalloc": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
+    "iwf_eigensolve": (_i, [_vp, C.POINTER(iwf_solve_opts), _vp, C.POINTER(C.c_double), _vp,
+                            C.POINTER(C.c_double), C.POINTER(iwf_solve_info), _vp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _fn = getattr(lib, _name)

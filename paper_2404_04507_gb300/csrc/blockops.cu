@@ -1,0 +1,725 @@
+// Block kernels of the eigensolver (declarations and layout conventions in blockops.cuh).
+#include <cmath>
+
+#include "blockops.cuh"
+
+namespace iwf {
+
+namespace {
+
+constexpr int kGramRows = 16;      // rows staged per Gram tile
+constexpr int kGramThreads = 256;  // 16 x 16 threads, 3 x 3 outputs each -> up to 48 x 48
+
+template <typename T> struct Acc { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+// G_partial[cta] = sum over this CTA's rows of conj(A_i,a) * B_i,c
+template <typename T>
+__global__ void __launch_bounds__(kGramThreads)
+gram_kernel(BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
+  using V2 = typename Cplx<T>::type;
+  using AT = typename Acc<T>::type;
+  __shared__ V2 sa[kGramRows][kMaxSmall + 1];
+  __shared__ V2 sb[kGramRows][kMaxSmall + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double sumr[3][3], sumi[3][3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+#pragma unroll
+    for (int v = 0; v < 3; ++v) { sumr[u][v] = 0; sumi[u][v] = 0; }
+  const long long ntiles = (N + kGramRows - 1) / kGramRows;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long r0 = t * kGramRows;
+    for (int e = threadIdx.x; e < kGramRows * ma; e += blockDim.x) {
+      const int k = e / kGramRows, r = e % kGramRows;
+      V2 v; v.x = 0; v.y = 0;
+      if (r0 + r < N) v = col_ptr<T>(A, k, N)[r0 + r];
+      sa[r][k] = v;
+    }
+    for (int e = threadIdx.x; e < kGramRows * mb; e += blockDim.x) {
+      const int k = e / kGramRows, r = e % kGramRows;
+      V2 v; v.x = 0; v.y = 0;
+      if (r0 + r < N) v = col_ptr<T>(B, k, N)[r0 + r];
+      sb[r][k] = v;
+    }
+    __syncthreads();
+    AT accr[3][3], acci[3][3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) { accr[u][v] = 0; acci[u][v] = 0; }
+    for (int r = 0; r < kGramRows; ++r) {
+      V2 av[3], bv[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int a = ty + 16 * u, c = tx + 16 * u;
+        av[u] = a < ma ? sa[r][a] : V2{0, 0};
+        bv[u] = c < mb ? sb[r][c] : V2{0, 0};
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          // conj(a) * b
+          accr[u][v] += (AT)av[u].x * (AT)bv[v].x + (AT)av[u].y * (AT)bv[v].y;
+          acci[u][v] += (AT)av[u].x * (AT)bv[v].y - (AT)av[u].y * (AT)bv[v].x;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) { sumr[u][v] += (double)accr[u][v]; sumi[u][v] += (double)acci[u][v]; }
+    __syncthreads();
+  }
+  double2* out = partial + (size_t)blockIdx.x * ma * mb;
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const int a = ty + 16 * u, c = tx + 16 * v;
+      if (a < ma && c < mb) out[a * mb + c] = make_double2(sumr[u][v], sumi[u][v]);
+    }
+}
+
+// Sum the per-CTA partials in a fixed order (deterministic).
+__global__ void reduce_partials(const double2* partial, int slots, int count, double2* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  double re = 0, im = 0;
+  for (int s = 0; s < slots; ++s) {
+    const double2 v = partial[(size_t)s * count + e];
+    re += v.x; im += v.y;
+  }
+  out[e] = make_double2(re, im);
+}
+
+constexpr int kUpdThreads = 256;
+
+// out1[:, j] (=|-=) sum_k S[:, k] C1[k, j]; out2 likewise with C2. C row-major m x q.
+template <typename T, bool SUB>
+__global__ void __launch_bounds__(kUpdThreads)
+update_kernel(BlockList S, int m, long long N, const double2* C1, const double2* C2, int q,
+              typename Cplx<T>::type* out1, typename Cplx<T>::type* out2) {
+  using V2 = typename Cplx<T>::type;
+  using AT = typename Acc<T>::type;
+  __shared__ double2 sc1[kMaxSmall * kMaxBlock];
+  __shared__ double2 sc2[kMaxSmall * kMaxBlock];
+  constexpr int rows = kUpdThreads / kMaxBlock;  // 16 rows per tile, one thread per (row, j)
+  __shared__ V2 ss[rows][kMaxSmall + 1];
+  for (int e = threadIdx.x; e < m * q; e += blockDim.x) {
+    sc1[e] = C1[e];
+    if (C2) sc2[e] = C2[e];
+  }
+  const int r = threadIdx.x / kMaxBlock, j = threadIdx.x % kMaxBlock;
+  const long long ntiles = (N + rows - 1) / rows;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long r0 = t * rows;
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+      const int k = e / rows, rr = e % rows;
+      V2 v; v.x = 0; v.y = 0;
+      if (r0 + rr < N) v = col_ptr<T>(S, k, N)[r0 + rr];
+      ss[rr][k] = v;
+    }
+    __syncthreads();
+    if (j < q && r0 + r < N) {
+      AT a1r = 0, a1i = 0, a2r = 0, a2i = 0;
+      for (int k = 0; k < m; ++k) {
+        const V2 sv = ss[r][k];
+        const double2 c1 = sc1[k * q + j];
+        a1r += (AT)sv.x * (AT)c1.x - (AT)sv.y * (AT)c1.y;
+        a1i += (AT)sv.x * (AT)c1.y + (AT)sv.y * (AT)c1.x;
+        if (C2) {
+          const double2 c2 = sc2[k * q + j];
+          a2r += (AT)sv.x * (AT)c2.x - (AT)sv.y * (AT)c2.y;
+          a2i += (AT)sv.x * (AT)c2.y + (AT)sv.y * (AT)c2.x;
+        }
+      }
+      const size_t gi = (size_t)j * N + r0 + r;
+      if (SUB) {
+        V2 o = out1[gi];
+        o.x = (T)((AT)o.x - a1r); o.y = (T)((AT)o.y - a1i);
+        out1[gi] = o;
+      } else {
+        V2 o; o.x = (T)a1r; o.y = (T)a1i;
+        out1[gi] = o;
+        if (C2) { V2 o2; o2.x = (T)a2r; o2.y = (T)a2i; out2[gi] = o2; }
+      }
+    }
+  }
+}
+
+constexpr int kResThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kResThreads)
+residual_kernel(const typename Cplx<T>::type* X, const typename Cplx<T>::type* HX,
+                const double* theta, const T* M, typename Cplx<T>::type* W, long long N, int b,
+                double* partial) {
+  using V2 = typename Cplx<T>::type;
+  using AT = typename Acc<T>::type;
+  __shared__ double red[kResThreads / 32][kMaxBlock];
+  AT acc[kMaxBlock];
+#pragma unroll
+  for (int j = 0; j < kMaxBlock; ++j) acc[j] = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T mi = M[i];
+#pragma unroll
+    for (int j = 0; j < kMaxBlock; ++j) {
+      if (j >= b) break;
+      const size_t gi = (size_t)j * N + i;
+      const V2 x = X[gi], h = HX[gi];
+      const T th = (T)theta[j];
+      V2 r; r.x = h.x - th * x.x; r.y = h.y - th * x.y;
+      acc[j] += (AT)r.x * (AT)r.x + (AT)r.y * (AT)r.y;
+      V2 w; w.x = mi * r.x; w.y = mi * r.y;
+      W[gi] = w;
+    }
+  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+  for (int j = 0; j < kMaxBlock; ++j) {
+    if (j >= b) break;
+    double v = (double)acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < b) {
+    double v = 0;
+    for (int w = 0; w < kResThreads / 32; ++w) v += red[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * b + threadIdx.x] = v;
+  }
+}
+
+__global__ void resid_finish(const double* partial, int slots, int b, double* resid) {
+  const int j = threadIdx.x;
+  if (j >= b) return;
+  double s = 0;
+  for (int c = 0; c < slots; ++c) s += partial[(size_t)c * b + j];
+  resid[j] = sqrt(s);
+}
+
+// ---------------------------------------------------------------------------------------
+// One-CTA dense Hermitian eigensolver: parallel cyclic Jacobi (round-robin pairing), FP64.
+// A (n x n, row-major, leading dimension ld) is overwritten; V receives the eigenvectors.
+constexpr int kSmallThreads = 512;
+
+struct SmallShared {
+  double2 A[kMaxSmall * kMaxSmall];
+  double2 V[kMaxSmall * kMaxSmall];
+  double2 B[kMaxSmall * kMaxSmall];
+  double w[kMaxSmall];
+  double rc[kMaxSmall / 2 + 1], rs[kMaxSmall / 2 + 1];
+  double2 ph[kMaxSmall / 2 + 1];
+  int rp[kMaxSmall / 2 + 1], rq[kMaxSmall / 2 + 1];
+  int idx[kMaxSmall];
+  int perm[kMaxSmall];
+  double red[kSmallThreads / 32];
+  int flag;
+  int rot;
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Eigen-decomposition of the Hermitian n x n matrix in sh.A (row-major, ld = n).
+// On return sh.w holds ascending eigenvalues and sh.V (row-major) the eigenvectors as columns.
+__device__ void jacobi_eig(SmallShared& sh, int n) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    sh.V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    // symmetrise: A = (A + A^H)/2
+    if (i < j) {
+      const double2 a = sh.A[i * n + j], c = sh.A[j * n + i];
+      const double2 m = make_double2(0.5 * (a.x + c.x), 0.5 * (a.y - c.y));
+      sh.A[i * n + j] = m;
+      sh.A[j * n + i] = cconj(m);
+    } else if (i == j) {
+      sh.A[e].y = 0.0;
+    }
+  }
+  __syncthreads();
+  if (n == 1) {
+    if (tid == 0) sh.w[0] = sh.A[0].x;
+    __syncthreads();
+    return;
+  }
+  const int ne = n + (n & 1);       // players, with one dummy when n is odd
+  const int np = ne / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    // convergence: off-diagonal Frobenius norm relative to the whole matrix
+    double off = 0, tot = 0;
+    for (int e = tid; e < n * n; e += nt) {
+      const double2 a = sh.A[e];
+      const double v = a.x * a.x + a.y * a.y;
+      tot += v;
+      if (e / n != e % n) off += v;
+    }
+    off = block_sum(off, sh.red);
+    tot = block_sum(tot, sh.red);
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    if (tid == 0) sh.rot = 0;
+    __syncthreads();
+    for (int round = 0; round < ne - 1; ++round) {
+      if (tid < np) {
+        const int k = tid;
+        const int posa = k, posb = ne - 1 - k;
+        const int p = posa == 0 ? 0 : ((posa - 1 + round) % (ne - 1)) + 1;
+        const int q = ((posb - 1 + round) % (ne - 1)) + 1;
+        double c = 1.0, s = 0.0;
+        double2 eph = make_double2(1.0, 0.0);   // e^{-i phi}
+        int pp = p < q ? p : q, qq = p < q ? q : p;
+        if (qq < n) {
+          const double2 apq = sh.A[pp * n + qq];
+          const double r = hypot(apq.x, apq.y);
+          const double a = sh.A[pp * n + pp].x, bq = sh.A[qq * n + qq].x;
+          if (r > 1e-300 && r > 1e-18 * sqrt(fabs(a * bq))) {
+            sh.rot = 1;
+            eph = make_double2(apq.x / r, -apq.y / r);
+            const double tau = (bq - a) / (2.0 * r);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        } else {
+          pp = -1;
+        }
+        sh.rc[k] = c; sh.rs[k] = s; sh.ph[k] = eph; sh.rp[k] = pp; sh.rq[k] = qq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < n * np; e += nt) {
+        const int i = e / np, k = e % np;
+        const int p = sh.rp[k];
+        if (p < 0 || sh.rs[k] == 0.0) continue;
+        const int q = sh.rq[k];
+        const double c = sh.rc[k], s = sh.rs[k];
+        const double2 eph = sh.ph[k];
+        {
+          const double2 aip = sh.A[i * n + p], aiq = sh.A[i * n + q];
+          const double2 t = cmul(aiq, eph);
+          sh.A[i * n + p] = make_double2(c * aip.x - s * t.x, c * aip.y - s * t.y);
+          sh.A[i * n + q] = make_double2(s * aip.x + c * t.x, s * aip.y + c * t.y);
+        }
+        {
+          const double2 vip = sh.V[i * n + p], viq = sh.V[i * n + q];
+          const double2 t = cmul(viq, eph);
+          sh.V[i * n + p] = make_double2(c * vip.x - s * t.x, c * vip.y - s * t.y);
+          sh.V[i * n + q] = make_double2(s * vip.x + c * t.x, s * vip.y + c * t.y);
+        }
+      }
+      __syncthreads();
+      // rows: A <- J^H A
+      for (int e = tid; e < n * np; e += nt) {
+        const int j = e / np, k = e % np;
+        const int p = sh.rp[k];
+        if (p < 0 || sh.rs[k] == 0.0) continue;
+        const int q = sh.rq[k];
+        const double c = sh.rc[k], s = sh.rs[k];
+        const double2 ephc = cconj(sh.ph[k]);   // e^{+i phi}
+        const double2 apj = sh.A[p * n + j], aqj = sh.A[q * n + j];
+        const double2 t = cmul(aqj, ephc);
+        sh.A[p * n + j] = make_double2(c * apj.x - s * t.x, c * apj.y - s * t.y);
+        sh.A[q * n + j] = make_double2(s * apj.x + c * t.x, s * apj.y + c * t.y);
+      }
+      __syncthreads();
+    }
+    if (sh.rot == 0) break;
+    __syncthreads();
+  }
+  // sort ascending: rank of every eigenvalue (ties by index)
+  for (int i = tid; i < n; i += nt) sh.w[i] = sh.A[i * n + i].x;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    int rank = 0;
+    const double wi = sh.w[i];
+    for (int j = 0; j < n; ++j) {
+      const double wj = sh.w[j];
+      rank += (wj < wi) || (wj == wi && j < i);
+    }
+    sh.perm[rank] = i;
+  }
+  __syncthreads();
+  // B <- V[:, perm], then V <- B; eigenvalues permuted through A's diagonal
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, r = e % n;
+    sh.B[e] = sh.V[i * n + sh.perm[r]];
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) sh.V[e] = sh.B[e];
+  for (int r = tid; r < n; r += nt) sh.B[r] = make_double2(sh.A[sh.perm[r] * n + sh.perm[r]].x, 0.0);
+  __syncthreads();
+  for (int r = tid; r < n; r += nt) sh.w[r] = sh.B[r].x;
+  __syncthreads();
+}
+
+// Orthonormalising transform of a block from its Gram matrix (SVQB):
+// D = diag(G)^{-1/2}, D G D = U S U^H, T = D U S^{-1/2} restricted to S > drop * max(S).
+// Columns of T beyond the kept rank are zero and their mask entry is 0.
+__global__ void __launch_bounds__(kSmallThreads)
+svqb_kernel(const double2* G, int b, double drop, double2* T, int* mask, int* status) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  SmallShared& sh = *reinterpret_cast<SmallShared*>(raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < b; i += nt) {
+    const double g = G[i * b + i].x;
+    sh.w[i] = g > 1e-300 ? 1.0 / sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += nt) {
+    const int i = e / b, j = e % b;
+    const double2 g = G[e];
+    sh.A[e] = make_double2(g.x * sh.w[i] * sh.w[j], g.y * sh.w[i] * sh.w[j]);
+  }
+  for (int i = tid; i < b; i += nt) sh.idx[i] = 0;
+  __syncthreads();
+  // keep D in B's first row while the eigensolver reuses w
+  for (int i = tid; i < b; i += nt) sh.B[kMaxSmall * kMaxSmall - 1 - i] = make_double2(sh.w[i], 0);
+  __syncthreads();
+  jacobi_eig(sh, b);
+  const double smax = sh.w[b - 1];
+  for (int e = tid; e < b * b; e += nt) {
+    const int i = e / b, k = e % b;   // T[i][k]; eigenvalues ascending, keep the largest
+    const int col = b - 1 - k;        // output column k <- eigenpair b-1-k (descending)
+    const double sk = sh.w[col];
+    const double di = sh.B[kMaxSmall * kMaxSmall - 1 - i].x;
+    double2 t = make_double2(0, 0);
+    if (smax > 0 && sk > drop * smax) {
+      const double f = di / sqrt(sk);
+      const double2 u = sh.V[i * b + col];
+      t = make_double2(u.x * f, u.y * f);
+    }
+    T[e] = t;
+  }
+  for (int k = tid; k < b; k += nt) {
+    const double sk = sh.w[b - 1 - k];
+    mask[k] = (smax > 0 && sk > drop * smax) ? 1 : 0;
+  }
+  if (tid == 0 && status) *status = 0;
+}
+
+// Rayleigh-Ritz on the orthonormal basis S (m columns, `mask` marks the active ones):
+// eigenpairs of the compacted Hermitian A; theta and Cx (m x b) take the lowest b.
+// Cp: Cx with its first x_rows rows zeroed (the W and P parts), orthogonalised against Cx
+// and orthonormalised in the coefficient space, so that S Cp is orthonormal and orthogonal
+// to S Cx; dependent columns are zero with mask_p = 0.
+__global__ void __launch_bounds__(kSmallThreads)
+rr_kernel(const double2* Ain, int m, int b, const int* mask, int x_rows, double* theta,
+          double2* Cx, double2* Cp, int* mask_p, int* status) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  SmallShared& sh = *reinterpret_cast<SmallShared*>(raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    int na = 0;
+    for (int i = 0; i < m; ++i) if (mask[i]) sh.idx[na++] = i;
+    sh.flag = na;
+  }
+  __syncthreads();
+  const int na = sh.flag;
+  if (na < b) {
+    if (tid == 0) *status = 1;
+    return;
+  }
+  for (int e = tid; e < na * na; e += nt) {
+    const int i = e / na, j = e % na;
+    sh.A[e] = Ain[sh.idx[i] * m + sh.idx[j]];
+  }
+  __syncthreads();
+  jacobi_eig(sh, na);
+  // Cx (m x b): rows of inactive columns are zero
+  for (int e = tid; e < m * b; e += nt) Cx[e] = make_double2(0, 0);
+  __syncthreads();
+  for (int e = tid; e < na * b; e += nt) {
+    const int i = e / b, k = e % b;
+    Cx[sh.idx[i] * b + k] = sh.V[i * na + k];
+  }
+  for (int k = tid; k < b; k += nt) theta[k] = sh.w[k];
+  __syncthreads();
+  __threadfence_block();
+  // Cp: two rounds of (orthogonalise against Cx twice, then orthonormalise). The second
+  // round acts on unit columns, so the rounding left by normalising tiny first-round
+  // columns (norm down to 1e-12) cannot survive as a loss of orthogonality to Cx.
+  for (int rep = 0; rep < 2; ++rep) {
+    for (int e = tid; e < m * b; e += nt) {
+      const double2 c = Cx[e];
+      sh.A[e] = c;
+      sh.B[e] = rep ? Cp[e] : ((e / b) < x_rows ? make_double2(0, 0) : c);
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int e = tid; e < b * b; e += nt) {
+        const int r = e / b, c = e % b;
+        double2 s = make_double2(0, 0);
+        for (int i = 0; i < m; ++i) {
+          const double2 t = cmul(cconj(sh.A[i * b + r]), sh.B[i * b + c]);
+          s.x += t.x; s.y += t.y;
+        }
+        sh.V[e] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * b; e += nt) {
+        const int i = e / b, c = e % b;
+        double2 s = make_double2(0, 0);
+        for (int r = 0; r < b; ++r) {
+          const double2 t = cmul(sh.A[i * b + r], sh.V[r * b + c]);
+          s.x += t.x; s.y += t.y;
+        }
+        sh.V[b * b + e] = make_double2(sh.B[e].x - s.x, sh.B[e].y - s.y);
+      }
+      __syncthreads();
+      for (int e = tid; e < m * b; e += nt) sh.B[e] = sh.V[b * b + e];
+      __syncthreads();
+    }
+    // Gram of Cp, then its SVQB transform in the coefficient space
+    for (int e = tid; e < b * b; e += nt) {
+      const int r = e / b, c = e % b;
+      double2 s = make_double2(0, 0);
+      for (int i = 0; i < m; ++i) {
+        const double2 t = cmul(cconj(sh.B[i * b + r]), sh.B[i * b + c]);
+        s.x += t.x; s.y += t.y;
+      }
+      sh.V[b * b + m * b + e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * b; e += nt) Cp[e] = sh.B[e];
+    for (int e = tid; e < b * b; e += nt) sh.A[e] = sh.V[b * b + m * b + e];
+    __syncthreads();
+    jacobi_eig(sh, b);
+    // keep columns of norm > 1e-12 in the first round, near-unit columns in the second
+    const double keep = rep ? 1e-2 : 1e-24;
+    for (int e = tid; e < b * b; e += nt) {
+      const int i = e / b, k = e % b;
+      const int col = b - 1 - k;
+      const double sk = sh.w[col];
+      double2 t = make_double2(0, 0);
+      if (sk > keep) {
+        const double f = 1.0 / sqrt(sk);
+        const double2 u = sh.V[i * b + col];
+        t = make_double2(u.x * f, u.y * f);
+      }
+      sh.A[e] = t;
+    }
+    for (int k = tid; k < b; k += nt) mask_p[k] = sh.w[b - 1 - k] > keep ? 1 : 0;
+    __syncthreads();
+    for (int e = tid; e < m * b; e += nt) sh.B[e] = Cp[e];
+    __syncthreads();
+    for (int e = tid; e < m * b; e += nt) {
+      const int i = e / b, c = e % b;
+      double2 s = make_double2(0, 0);
+      for (int r = 0; r < b; ++r) {
+        const double2 t = cmul(sh.B[i * b + r], sh.A[r * b + c]);
+        s.x += t.x; s.y += t.y;
+      }
+      Cp[e] = s;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *status = 0;
+}
+
+template <typename T>
+__global__ void precond_kernel(const double* lam, double shift, double off2, long long N, T* M) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double h = lam[i] + shift;
+  M[i] = (T)(h / (h * h + off2));
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin* in, Tout* out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (Tout)in[i];
+}
+
+// splitmix64 (Steele, Lea, Flood 2014) as a counter-based generator of start vectors.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void random_kernel(typename Cplx<T>::type* X, long long count, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long a = splitmix64(seed ^ (2ull * (unsigned long long)i));
+    const unsigned long long c = splitmix64(seed ^ (2ull * (unsigned long long)i + 1ull));
+    typename Cplx<T>::type v;
+    v.x = (T)((double)(a >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    v.y = (T)((double)(c >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    X[i] = v;
+  }
+}
+
+__global__ void mask_kernel(int* mask, int b, int value) {
+  if ((int)threadIdx.x < b) mask[threadIdx.x] = value;
+}
+
+int grid_for(long long work, int per_block) {
+  long long g = (work + per_block - 1) / per_block;
+  if (g > 4 * 152) g = 4 * 152;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+template <typename T>
+iwf_status gram(const BlockList& A, const BlockList& B, long long N, double2* out,
+                double2* partial, int partial_slots, cudaStream_t s) {
+  const int ma = A.nb * A.b, mb = B.nb * B.b;
+  if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram: too many columns");
+  int g = grid_for(N, kGramRows);
+  if (g > partial_slots) g = partial_slots;
+  gram_kernel<T><<<g, kGramThreads, 0, s>>>(A, B, ma, mb, N, partial);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  const int cnt = ma * mb;
+  reduce_partials<<<(cnt + 255) / 256, 256, 0, s>>>(partial, g, cnt, out);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template <typename T>
+iwf_status block_update(const BlockList& S, long long N, const double2* C1, const double2* C2,
+                        int q, void* out1, void* out2, bool subtract, cudaStream_t s) {
+  using V2 = typename Cplx<T>::type;
+  const int m = S.nb * S.b;
+  if (m > kMaxSmall || q > kMaxBlock || q < 1) return fail(IWF_ERR_ARG, "block_update: shape");
+  const int g = grid_for(N, kUpdThreads / kMaxBlock);
+  if (subtract)
+    update_kernel<T, true><<<g, kUpdThreads, 0, s>>>(S, m, N, C1, nullptr, q,
+                                                     reinterpret_cast<V2*>(out1), nullptr);
+  else
+    update_kernel<T, false><<<g, kUpdThreads, 0, s>>>(S, m, N, C1, C2, q,
+                                                      reinterpret_cast<V2*>(out1),
+                                                      reinterpret_cast<V2*>(out2));
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template <typename T>
+iwf_status residual_precond(const void* X, const void* HX, const double* theta, const T* M,
+                            void* W, long long N, int b, double* partial, int partial_slots,
+                            double* resid, cudaStream_t s) {
+  using V2 = typename Cplx<T>::type;
+  int g = grid_for(N, kResThreads);
+  if (g > partial_slots) g = partial_slots;
+  residual_kernel<T><<<g, kResThreads, 0, s>>>(reinterpret_cast<const V2*>(X),
+                                               reinterpret_cast<const V2*>(HX), theta, M,
+                                               reinterpret_cast<V2*>(W), N, b, partial);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  resid_finish<<<1, 32, 0, s>>>(partial, g, b, resid);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+static iwf_status small_smem_attr(const void* fn) {
+  IWF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(SmallShared)));
+  return IWF_OK;
+}
+
+iwf_status svqb_small(const double2* G, int b, double drop, double2* T, int* mask, int* status,
+                      cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) { IWF_TRY(small_smem_attr((const void*)svqb_kernel)); attr = true; }
+  svqb_kernel<<<1, kSmallThreads, sizeof(SmallShared), s>>>(G, b, drop, T, mask, status);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+iwf_status rayleigh_ritz_small(const double2* A, int m, int b, const int* mask, int x_rows,
+                               double* theta, double2* Cx, double2* Cp, int* mask_p,
+                               int* status, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) { IWF_TRY(small_smem_attr((const void*)rr_kernel)); attr = true; }
+  rr_kernel<<<1, kSmallThreads, sizeof(SmallShared), s>>>(A, m, b, mask, x_rows, theta, Cx, Cp,
+                                                          mask_p, status);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template <typename T>
+iwf_status precond_diag(const double* lam, double shift, double off2, long long N, T* M,
+                        cudaStream_t s) {
+  precond_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(lam, shift, off2, N, M);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template <typename Tin, typename Tout>
+iwf_status convert_block(const void* in, void* out, long long count, cudaStream_t s) {
+  convert_kernel<Tin, Tout><<<grid_for(count, 256), 256, 0, s>>>(
+      reinterpret_cast<const Tin*>(in), reinterpret_cast<Tout*>(out), count);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template <typename T>
+iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cudaStream_t s) {
+  const long long count = N * b;
+  random_kernel<T><<<grid_for(count, 256), 256, 0, s>>>(
+      reinterpret_cast<typename Cplx<T>::type*>(X), count, seed);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+iwf_status set_mask(int* mask, int b, int value, cudaStream_t s) {
+  mask_kernel<<<1, 64, 0, s>>>(mask, b, value);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template iwf_status gram<double>(const BlockList&, const BlockList&, long long, double2*,
+                                 double2*, int, cudaStream_t);
+template iwf_status gram<float>(const BlockList&, const BlockList&, long long, double2*,
+                                double2*, int, cudaStream_t);
+template iwf_status block_update<double>(const BlockList&, long long, const double2*,
+                                         const double2*, int, void*, void*, bool, cudaStream_t);
+template iwf_status block_update<float>(const BlockList&, long long, const double2*,
+                                        const double2*, int, void*, void*, bool, cudaStream_t);
+template iwf_status residual_precond<double>(const void*, const void*, const double*,
+                                             const double*, void*, long long, int, double*, int,
+                                             double*, cudaStream_t);
+template iwf_status residual_precond<float>(const void*, const void*, const double*,
+                                            const float*, void*, long long, int, double*, int,
+                                            double*, cudaStream_t);
+template iwf_status precond_diag<double>(const double*, double, double, long long, double*,
+                                         cudaStream_t);
+template iwf_status precond_diag<float>(const double*, double, double, long long, float*,
+                                        cudaStream_t);
+template iwf_status convert_block<double, float>(const void*, void*, long long, cudaStream_t);
+template iwf_status convert_block<float, double>(const void*, void*, long long, cudaStream_t);
+template iwf_status random_block<double>(void*, long long, int, unsigned long long, cudaStream_t);
+template iwf_status random_block<float>(void*, long long, int, unsigned long long, cudaStream_t);
+
+}  // namespace iwf

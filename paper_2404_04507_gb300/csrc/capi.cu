@@ -236,6 +236,14 @@ iwf_status iwf_apply_profile(iwf_plan* p, int precision, const void* psi, void* 
 
 long long iwf_kernel_launches(void) { return launch_count(); }
 
+iwf_status iwf_eigensolve(iwf_plan* p, const iwf_solve_opts* opts, const void* X0, double* evals,
+                          void* evecs, double* resid, iwf_solve_info* info, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_eigensolve: NULL plan");
+  DeviceGuard guard(p->device);
+  return eigensolve_impl(p, opts, X0, evals, evecs, resid, info, (cudaStream_t)stream);
+}
+
 iwf_status iwf_apply_noalloc(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                              void* stream) {
   if (!p) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: NULL plan");

@@ -109,6 +109,8 @@ iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, i
                       cudaStream_t stream, PassTimer* timer = nullptr);
 iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                               cudaStream_t stream);
+iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
+                           void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties
