@@ -168,6 +168,33 @@ def cpu_oracle_rate(pb, budget_s: float = 12.0, max_vectors: int = 64):
     return done * win.N / dt, done, dt
 
 
+SOLVE_RUNS = [("iwfpm_f64", "iwfpm", "f64"), ("iwfpm_mixed", "iwfpm", "c64"),
+              ("pm_f64", "pm", "f64")]
+
+
+def time_solves(iwf, torch, local, nev=16, block=24, eps=EPS, maxit=600, runs=None):
+    """Time to nev eigenpairs at residual 1e-10 on the 32^4 grid: IWFPM (FP64, then the
+    complex64-then-FP64 mixed mode) and PM on the box [-16,16)^4 (same DOF), FP64."""
+    out = {"nev": nev, "block": block, "tol": 1e-10, "eps": eps}
+    for key, method, prec in (runs or SOLVE_RUNS):
+        pb = W.config_moire(eps=eps, method=method)
+        plan = iwf.Plan(pb.P, pb.K, pb.L, method=method, device=local)
+        plan.set_potential(pb.modes, pb.coef)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ev, X, res, info = plan.eigensolve(nev, block=block, tol=1e-10, maxit=maxit,
+                                           precision=prec, seed=7, raise_noconv=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[key] = {"seconds": e0.elapsed_time(e1) / 1e3, "iters": info["iters"],
+                    "iters_c64": info["iters_c64"], "applies": info["applies"],
+                    "converged": bool(info["converged"]), "max_resid": info["max_resid"],
+                    "lambda_0": float(ev[0]), "lambda_last": float(ev[-1])}
+        plan.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -194,6 +221,16 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+    return 0
+
+
+def run_solve_only(args):
+    """--solve-only: one eigensolve (for profiling); prints its timing object."""
+    import torch
+    import paper_2404_04507_gb300 as iwf
+    runs = [r for r in SOLVE_RUNS if r[0] == args.solve_run]
+    out = time_solves(iwf, torch, 0, maxit=args.solve_maxit, runs=runs)
+    print(json.dumps(out))
     return 0
 
 
@@ -313,6 +350,8 @@ def run_ours(args):
     e2e = {"value": pts * ws / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
 
+    solve = None if args.no_solve else time_solves(iwf, torch, local)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -332,7 +371,7 @@ def run_ours(args):
                    "parallelism": f"replicas{ws}",
                    "l2": "inputs 268 MB > 129 MB L2; no flush needed"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "c64_apply": c64,
+        "clocks": clk, "c64_apply": c64, "solve": solve,
     }
     print(json.dumps(line))
     if ws > 1:
@@ -347,8 +386,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the time-to-eigenpairs measurement (IWFPM vs PM)")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="run one eigensolve and print its timing (profiling aid)")
+    ap.add_argument("--solve-run", default="iwfpm_f64", choices=[r[0] for r in SOLVE_RUNS])
+    ap.add_argument("--solve-maxit", type=int, default=600)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)
+    if args.solve_only:
+        return run_solve_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

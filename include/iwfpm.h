@@ -131,7 +131,7 @@ iwf_status iwf_preconditioner(const iwf_plan* plan, double* M, double* sigma);
 
 typedef struct {
   int nev;          /* eigenpairs wanted, 1 <= nev <= block                                 */
-  int block;        /* LOBPCG block size b (0: b = nev), at most 16                          */
+  int block;        /* LOBPCG block size b (0: b = nev), at most 24                          */
   int maxit;        /* iteration limit over both phases (0: 1000)                            */
   double tol;       /* stop when |H~x_i - lambda_i x_i|_2 <= tol for i < nev, |x_i|_2 = 1
                        (0: 1e-10)                                                           */

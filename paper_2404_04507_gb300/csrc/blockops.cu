@@ -8,25 +8,28 @@ namespace iwf {
 namespace {
 
 constexpr int kGramRows = 16;      // rows staged per Gram tile
-constexpr int kGramThreads = 256;  // 16 x 16 threads, 3 x 3 outputs each -> up to 48 x 48
+constexpr int kGramTx = 24;        // 24 x 24 threads, 3 x 3 outputs each -> up to 72 x 72
+constexpr int kGramThreads = kGramTx * kGramTx;
 
 template <typename T> struct Acc { using type = double; };
 template <> struct Acc<float> { using type = float; };
 
-// G_partial[cta] = sum over this CTA's rows of conj(A_i,a) * B_i,c
-template <typename T>
+// G_partial[cta] = sum over this CTA's rows of conj(A_i,a) * B_i,c.
+// 24 x 24 threads; each owns a U x V micro-tile (outputs ty + 24u, tx + 24v), so the
+// launch picks U = ceil(ma/24), V = ceil(mb/24) and no thread multiplies padding.
+template <typename T, int U, int V>
 __global__ void __launch_bounds__(kGramThreads)
 gram_kernel(BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
   __shared__ V2 sa[kGramRows][kMaxSmall + 1];
   __shared__ V2 sb[kGramRows][kMaxSmall + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double sumr[3][3], sumi[3][3];
+  const int tx = threadIdx.x % kGramTx, ty = threadIdx.x / kGramTx;
+  double sumr[U][V], sumi[U][V];
 #pragma unroll
-  for (int u = 0; u < 3; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 3; ++v) { sumr[u][v] = 0; sumi[u][v] = 0; }
+    for (int v = 0; v < V; ++v) { sumr[u][v] = 0; sumi[u][v] = 0; }
   const long long ntiles = (N + kGramRows - 1) / kGramRows;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const long long r0 = t * kGramRows;
@@ -43,40 +46,40 @@ gram_kernel(BlockList A, BlockList B, int ma, int mb, long long N, double2* part
       sb[r][k] = v;
     }
     __syncthreads();
-    AT accr[3][3], acci[3][3];
+    AT accr[U][V], acci[U][V];
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int v = 0; v < 3; ++v) { accr[u][v] = 0; acci[u][v] = 0; }
+      for (int v = 0; v < V; ++v) { accr[u][v] = 0; acci[u][v] = 0; }
     for (int r = 0; r < kGramRows; ++r) {
-      V2 av[3], bv[3];
+      V2 av[U], bv[V];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int a = ty + 16 * u, c = tx + 16 * u;
-        av[u] = a < ma ? sa[r][a] : V2{0, 0};
-        bv[u] = c < mb ? sb[r][c] : V2{0, 0};
-      }
+      for (int u = 0; u < U; ++u) av[u] = sa[r][min(ty + kGramTx * u, kMaxSmall)];
 #pragma unroll
-      for (int u = 0; u < 3; ++u)
+      for (int v = 0; v < V; ++v) bv[v] = sb[r][min(tx + kGramTx * v, kMaxSmall)];
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          // conj(a) * b
-          accr[u][v] += (AT)av[u].x * (AT)bv[v].x + (AT)av[u].y * (AT)bv[v].y;
-          acci[u][v] += (AT)av[u].x * (AT)bv[v].y - (AT)av[u].y * (AT)bv[v].x;
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          // conj(a) * b: re = ax bx + ay by, im = ax by - ay bx
+          accr[u][v] = fma((AT)av[u].x, (AT)bv[v].x, accr[u][v]);
+          accr[u][v] = fma((AT)av[u].y, (AT)bv[v].y, accr[u][v]);
+          acci[u][v] = fma((AT)av[u].x, (AT)bv[v].y, acci[u][v]);
+          acci[u][v] = fma(-(AT)av[u].y, (AT)bv[v].x, acci[u][v]);
         }
     }
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int v = 0; v < 3; ++v) { sumr[u][v] += (double)accr[u][v]; sumi[u][v] += (double)acci[u][v]; }
+      for (int v = 0; v < V; ++v) { sumr[u][v] += (double)accr[u][v]; sumi[u][v] += (double)acci[u][v]; }
     __syncthreads();
   }
   double2* out = partial + (size_t)blockIdx.x * ma * mb;
 #pragma unroll
-  for (int u = 0; u < 3; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      const int a = ty + 16 * u, c = tx + 16 * v;
+    for (int v = 0; v < V; ++v) {
+      const int a = ty + kGramTx * u, c = tx + kGramTx * v;
       if (a < ma && c < mb) out[a * mb + c] = make_double2(sumr[u][v], sumi[u][v]);
     }
 }
@@ -93,7 +96,8 @@ __global__ void reduce_partials(const double2* partial, int slots, int count, do
   out[e] = make_double2(re, im);
 }
 
-constexpr int kUpdThreads = 256;
+constexpr int kUpdRows = 16;
+constexpr int kUpdThreads = kUpdRows * kMaxBlock;
 
 // out1[:, j] (=|-=) sum_k S[:, k] C1[k, j]; out2 likewise with C2. C row-major m x q.
 template <typename T, bool SUB>
@@ -102,15 +106,16 @@ update_kernel(BlockList S, int m, long long N, const double2* C1, const double2*
               typename Cplx<T>::type* out1, typename Cplx<T>::type* out2) {
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
-  __shared__ double2 sc1[kMaxSmall * kMaxBlock];
-  __shared__ double2 sc2[kMaxSmall * kMaxBlock];
-  constexpr int rows = kUpdThreads / kMaxBlock;  // 16 rows per tile, one thread per (row, j)
+  extern __shared__ __align__(16) unsigned char upd_raw[];
+  double2* sc1 = reinterpret_cast<double2*>(upd_raw);
+  double2* sc2 = sc1 + kMaxSmall * kMaxBlock;
+  constexpr int rows = kUpdRows;                  // one thread per (row, j)
   __shared__ V2 ss[rows][kMaxSmall + 1];
   for (int e = threadIdx.x; e < m * q; e += blockDim.x) {
     sc1[e] = C1[e];
     if (C2) sc2[e] = C2[e];
   }
-  const int r = threadIdx.x / kMaxBlock, j = threadIdx.x % kMaxBlock;
+  const int r = threadIdx.x / kMaxBlock, j = threadIdx.x % kMaxBlock;  // r < kUpdRows
   const long long ntiles = (N + rows - 1) / rows;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const long long r0 = t * rows;
@@ -127,12 +132,16 @@ update_kernel(BlockList S, int m, long long N, const double2* C1, const double2*
       for (int k = 0; k < m; ++k) {
         const V2 sv = ss[r][k];
         const double2 c1 = sc1[k * q + j];
-        a1r += (AT)sv.x * (AT)c1.x - (AT)sv.y * (AT)c1.y;
-        a1i += (AT)sv.x * (AT)c1.y + (AT)sv.y * (AT)c1.x;
+        a1r = fma((AT)sv.x, (AT)c1.x, a1r);
+        a1r = fma(-(AT)sv.y, (AT)c1.y, a1r);
+        a1i = fma((AT)sv.x, (AT)c1.y, a1i);
+        a1i = fma((AT)sv.y, (AT)c1.x, a1i);
         if (C2) {
           const double2 c2 = sc2[k * q + j];
-          a2r += (AT)sv.x * (AT)c2.x - (AT)sv.y * (AT)c2.y;
-          a2i += (AT)sv.x * (AT)c2.y + (AT)sv.y * (AT)c2.x;
+          a2r = fma((AT)sv.x, (AT)c2.x, a2r);
+          a2r = fma(-(AT)sv.y, (AT)c2.y, a2r);
+          a2i = fma((AT)sv.x, (AT)c2.y, a2i);
+          a2i = fma((AT)sv.y, (AT)c2.x, a2i);
         }
       }
       const size_t gi = (size_t)j * N + r0 + r;
@@ -158,7 +167,7 @@ residual_kernel(const typename Cplx<T>::type* X, const typename Cplx<T>::type* H
                 double* partial) {
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
-  __shared__ double red[kResThreads / 32][kMaxBlock];
+  __shared__ double red[kResThreads / 32][kMaxBlock];  // b <= kMaxBlock
   AT acc[kMaxBlock];
 #pragma unroll
   for (int j = 0; j < kMaxBlock; ++j) acc[j] = 0;
@@ -209,8 +218,10 @@ constexpr int kSmallThreads = 512;
 struct SmallShared {
   double2 A[kMaxSmall * kMaxSmall];
   double2 V[kMaxSmall * kMaxSmall];
-  double2 B[kMaxSmall * kMaxSmall];
+  double2 B[kMaxSmall * kMaxBlock];   // m x b scratch (the P coefficients)
   double w[kMaxSmall];
+  double w2[kMaxSmall];
+  double d[kMaxSmall];
   double rc[kMaxSmall / 2 + 1], rs[kMaxSmall / 2 + 1];
   double2 ph[kMaxSmall / 2 + 1];
   int rp[kMaxSmall / 2 + 1], rq[kMaxSmall / 2 + 1];
@@ -344,28 +355,26 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
     __syncthreads();
   }
   // sort ascending: rank of every eigenvalue (ties by index)
-  for (int i = tid; i < n; i += nt) sh.w[i] = sh.A[i * n + i].x;
+  for (int i = tid; i < n; i += nt) sh.w2[i] = sh.A[i * n + i].x;
   __syncthreads();
   for (int i = tid; i < n; i += nt) {
     int rank = 0;
-    const double wi = sh.w[i];
+    const double wi = sh.w2[i];
     for (int j = 0; j < n; ++j) {
-      const double wj = sh.w[j];
+      const double wj = sh.w2[j];
       rank += (wj < wi) || (wj == wi && j < i);
     }
     sh.perm[rank] = i;
   }
   __syncthreads();
-  // B <- V[:, perm], then V <- B; eigenvalues permuted through A's diagonal
+  // A (no longer needed) <- V[:, perm], then V <- A
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, r = e % n;
-    sh.B[e] = sh.V[i * n + sh.perm[r]];
+    sh.A[e] = sh.V[i * n + sh.perm[r]];
   }
+  for (int r = tid; r < n; r += nt) sh.w[r] = sh.w2[sh.perm[r]];
   __syncthreads();
-  for (int e = tid; e < n * n; e += nt) sh.V[e] = sh.B[e];
-  for (int r = tid; r < n; r += nt) sh.B[r] = make_double2(sh.A[sh.perm[r] * n + sh.perm[r]].x, 0.0);
-  __syncthreads();
-  for (int r = tid; r < n; r += nt) sh.w[r] = sh.B[r].x;
+  for (int e = tid; e < n * n; e += nt) sh.V[e] = sh.A[e];
   __syncthreads();
 }
 
@@ -387,10 +396,8 @@ svqb_kernel(const double2* G, int b, double drop, double2* T, int* mask, int* st
     const double2 g = G[e];
     sh.A[e] = make_double2(g.x * sh.w[i] * sh.w[j], g.y * sh.w[i] * sh.w[j]);
   }
-  for (int i = tid; i < b; i += nt) sh.idx[i] = 0;
-  __syncthreads();
-  // keep D in B's first row while the eigensolver reuses w
-  for (int i = tid; i < b; i += nt) sh.B[kMaxSmall * kMaxSmall - 1 - i] = make_double2(sh.w[i], 0);
+  // keep D while the eigensolver reuses w
+  for (int i = tid; i < b; i += nt) sh.d[i] = sh.w[i];
   __syncthreads();
   jacobi_eig(sh, b);
   const double smax = sh.w[b - 1];
@@ -398,7 +405,7 @@ svqb_kernel(const double2* G, int b, double drop, double2* T, int* mask, int* st
     const int i = e / b, k = e % b;   // T[i][k]; eigenvalues ascending, keep the largest
     const int col = b - 1 - k;        // output column k <- eigenpair b-1-k (descending)
     const double sk = sh.w[col];
-    const double di = sh.B[kMaxSmall * kMaxSmall - 1 - i].x;
+    const double di = sh.d[i];
     double2 t = make_double2(0, 0);
     if (smax > 0 && sk > drop * smax) {
       const double f = di / sqrt(sk);
@@ -589,7 +596,15 @@ iwf_status gram(const BlockList& A, const BlockList& B, long long N, double2* ou
   if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram: too many columns");
   int g = grid_for(N, kGramRows);
   if (g > partial_slots) g = partial_slots;
-  gram_kernel<T><<<g, kGramThreads, 0, s>>>(A, B, ma, mb, N, partial);
+  const int U = (ma + kGramTx - 1) / kGramTx, V = (mb + kGramTx - 1) / kGramTx;
+  switch (U * 4 + V) {
+#define IWF_GRAM(U_, V_) \
+    case U_ * 4 + V_: gram_kernel<T, U_, V_><<<g, kGramThreads, 0, s>>>(A, B, ma, mb, N, partial); break;
+    IWF_GRAM(1, 1) IWF_GRAM(1, 2) IWF_GRAM(1, 3) IWF_GRAM(2, 1) IWF_GRAM(2, 2) IWF_GRAM(2, 3)
+    IWF_GRAM(3, 1) IWF_GRAM(3, 2) IWF_GRAM(3, 3)
+#undef IWF_GRAM
+    default: return fail(IWF_ERR_ARG, "gram: shape");
+  }
   IWF_CUDA(cudaGetLastError());
   count_launch();
   const int cnt = ma * mb;
@@ -602,17 +617,29 @@ iwf_status gram(const BlockList& A, const BlockList& B, long long N, double2* ou
 template <typename T>
 iwf_status block_update(const BlockList& S, long long N, const double2* C1, const double2* C2,
                         int q, void* out1, void* out2, bool subtract, cudaStream_t s) {
+  // (the static attribute flags below are per instantiation of T)
   using V2 = typename Cplx<T>::type;
   const int m = S.nb * S.b;
   if (m > kMaxSmall || q > kMaxBlock || q < 1) return fail(IWF_ERR_ARG, "block_update: shape");
-  const int g = grid_for(N, kUpdThreads / kMaxBlock);
+  const int g = grid_for(N, kUpdRows);
+  const size_t dyn = 2 * sizeof(double2) * kMaxSmall * kMaxBlock;
+  static bool attr[2] = {false, false};
+  if (!attr[subtract]) {
+    if (subtract)
+      IWF_CUDA(cudaFuncSetAttribute(update_kernel<T, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    else
+      IWF_CUDA(cudaFuncSetAttribute(update_kernel<T, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    attr[subtract] = true;
+  }
   if (subtract)
-    update_kernel<T, true><<<g, kUpdThreads, 0, s>>>(S, m, N, C1, nullptr, q,
-                                                     reinterpret_cast<V2*>(out1), nullptr);
+    update_kernel<T, true><<<g, kUpdThreads, dyn, s>>>(S, m, N, C1, nullptr, q,
+                                                       reinterpret_cast<V2*>(out1), nullptr);
   else
-    update_kernel<T, false><<<g, kUpdThreads, 0, s>>>(S, m, N, C1, C2, q,
-                                                      reinterpret_cast<V2*>(out1),
-                                                      reinterpret_cast<V2*>(out2));
+    update_kernel<T, false><<<g, kUpdThreads, dyn, s>>>(S, m, N, C1, C2, q,
+                                                        reinterpret_cast<V2*>(out1),
+                                                        reinterpret_cast<V2*>(out2));
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;

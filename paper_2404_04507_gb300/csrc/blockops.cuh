@@ -13,7 +13,7 @@
 
 namespace iwf {
 
-constexpr int kMaxBlock = 16;              // b, the eigensolver block size
+constexpr int kMaxBlock = 24;              // b, the eigensolver block size
 constexpr int kMaxSmall = 3 * kMaxBlock;   // m = 3b, size of the Rayleigh-Ritz problem
 
 template <typename T> struct Cplx;

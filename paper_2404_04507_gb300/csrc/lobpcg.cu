@@ -236,7 +236,7 @@ iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0,
   const int nev = o->nev;
   const int b = o->block > 0 ? o->block : nev;
   if (nev < 1 || b < nev || b > kMaxBlock)
-    return fail(IWF_ERR_ARG, "iwf_eigensolve: need 1 <= nev <= block <= 16");
+    return fail(IWF_ERR_ARG, "iwf_eigensolve: need 1 <= nev <= block <= 24");
   if ((long long)3 * b > p->g.N) return fail(IWF_ERR_ARG, "iwf_eigensolve: window too small for the block");
   if (!evals || !evecs) return fail(IWF_ERR_ARG, "iwf_eigensolve: NULL output");
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_eigensolve: no potential set");

@@ -123,4 +123,4 @@ def test_eigensolve_argument_errors(iwf):
     with pytest.raises(capi.IwfError):
         plan.eigensolve(8, block=4)
     with pytest.raises(capi.IwfError):
-        plan.eigensolve(17, block=17)
+        plan.eigensolve(25, block=25)
