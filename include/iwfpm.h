@@ -172,6 +172,28 @@ iwf_status iwf_eigensolve(iwf_plan* plan, const iwf_solve_opts* opts, const void
                           void* stream);
 
 /*
+ * Lowest nev eigenpairs of nprob problems that share the plan's P, K, L and method but
+ * each have their own lifted potential (for example a sweep over potential strengths and
+ * phases). The problems advance in lockstep through the same kernels -- the apply takes
+ * each vector's potential table from its problem, Gram products and updates carry the
+ * problem in the grid, the small Rayleigh-Ritz problems run one CTA per problem -- and a
+ * converged problem drops out by a device flag. The steady-state iteration is captured
+ * into a CUDA graph and replayed. Same method, options and tolerance as iwf_eigensolve.
+ *   nmodes  host, nprob ints; m (sum(nmodes) * n ints), re, im (sum(nmodes) doubles): the
+ *           problems' mode lists, concatenated in problem order, as for iwf_set_potential.
+ *           Every mode must lie on a single lifted axis (IWF_ERR_UNSUPPORTED otherwise).
+ *   evals   host, nprob*nev (problem-major).  resid host, nprob*nev (may be NULL).
+ *   evecs   device, nprob*N*nev complex doubles (problem p at offset p*N*nev), or NULL.
+ *   iters   host, nprob ints (may be NULL): iterations each problem needed.
+ *   info    host (may be NULL): totals over the batch (iters = lockstep iterations).
+ * The start block is the seeded random one. nprob * block <= 65535. Synchronises `stream`.
+ */
+iwf_status iwf_batch_eigensolve(iwf_plan* plan, int nprob, const int* nmodes, const int* m,
+                                const double* re, const double* im, const iwf_solve_opts* opts,
+                                double* evals, void* evecs, double* resid, int* iters,
+                                iwf_solve_info* info, void* stream);
+
+/*
  * Same computation as iwf_apply, with CUDA events recorded on `stream` around every pass
  * kernel (pass A: inverse DFT along k_I with the gather; pass B: k_II inverse DFT, V,
  * k_II forward DFT; pass C: forward DFT along k_I with the scatter and Lambda psi).

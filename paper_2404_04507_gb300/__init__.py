@@ -163,6 +163,46 @@ class Plan:
         return evals, evecs, resid, out
 
 
+    def batch_eigensolve(self, potentials, nev, block=0, tol=1e-10, maxit=0, precision="f64",
+                         c64_tol=0.0, seed=1, want_vectors=False, stream=None,
+                         raise_noconv=True):
+        """iwf_batch_eigensolve over [(modes, coef), ...] sharing this plan's geometry.
+
+        Returns (evals (nprob, nev), evecs (nprob, nev, N) or None, resid, iters, info)."""
+        torch = _torch()
+        c = self._c
+        nprob = len(potentials)
+        nm = np.array([len(np.asarray(cf).reshape(-1)) for _, cf in potentials], dtype=np.int32)
+        modes = np.ascontiguousarray(np.concatenate(
+            [np.asarray(mm, dtype=np.int32).reshape(-1, self.n) for mm, _ in potentials]))
+        coef = np.concatenate([np.asarray(cf, dtype=np.complex128).reshape(-1)
+                               for _, cf in potentials])
+        re, im = np.ascontiguousarray(coef.real), np.ascontiguousarray(coef.imag)
+        opts = c.iwf_solve_opts(int(nev), int(block), int(maxit), float(tol),
+                                c.IWF_PREC_F64 if precision == "f64" else c.IWF_PREC_C64,
+                                float(c64_tol), int(seed))
+        evals = np.zeros((nprob, nev))
+        resid = np.zeros((nprob, nev))
+        iters = np.zeros(nprob, dtype=np.int32)
+        evecs = None
+        if want_vectors:
+            evecs = torch.empty((nprob, nev, self.N), dtype=torch.complex128,
+                                device=f"cuda:{self.device}")
+        info = c.iwf_solve_info()
+        st = c.iwf_batch_eigensolve(
+            self.handle, nprob, nm.ctypes.data_as(C.POINTER(C.c_int)),
+            modes.ctypes.data_as(C.POINTER(C.c_int)), re.ctypes.data_as(C.POINTER(C.c_double)),
+            im.ctypes.data_as(C.POINTER(C.c_double)), C.byref(opts),
+            evals.ctypes.data_as(C.POINTER(C.c_double)),
+            C.c_void_p(evecs.data_ptr()) if evecs is not None else None,
+            resid.ctypes.data_as(C.POINTER(C.c_double)), iters.ctypes.data_as(C.POINTER(C.c_int)),
+            C.byref(info), self._stream(stream))
+        if st != 0 and not (st == -7 and not raise_noconv):
+            c.check(st, "iwf_batch_eigensolve")
+        out = {f: getattr(info, f) for f, _ in c.iwf_solve_info._fields_}
+        return evals, evecs, resid, iters, out
+
+
 def kernel_launches() -> int:
     """Kernels launched by the CUDA library so far in this process."""
     from . import capi

@@ -70,6 +70,10 @@ _PROTOS = {
     "iwf_apply_noalloc": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_eigensolve": (_i, [_vp, C.POINTER(iwf_solve_opts), _vp, C.POINTER(C.c_double), _vp,
                             C.POINTER(C.c_double), C.POINTER(iwf_solve_info), _vp]),
+    "iwf_batch_eigensolve": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(iwf_solve_opts),
+                                  C.POINTER(C.c_double), _vp, C.POINTER(C.c_double),
+                                  C.POINTER(_i), C.POINTER(iwf_solve_info), _vp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _fn = getattr(lib, _name)

@@ -58,8 +58,9 @@ struct PassArgs {
   const void* psi;          // pass C only
   const void* lam;          // pass C only
   const int* lo;            // MII x d
-  PotDev pot;               // pass B only
+  PotDev pot;               // pass B only (tables); all passes (batch skipping)
   long long ld;             // element stride between vectors (= N)
+  int vec_base;             // index of the launch's first vector in the whole block
 };
 
 // Roll offset of axis a for outer tile index o: pencil element k* lives at (k* + off) mod len.
@@ -123,9 +124,9 @@ __device__ void axis_dispatch(typename Vec2<T>::type* tile, const PassArgs& a, i
   }
 }
 
-template <typename T> __device__ __forceinline__ T pot_tab(const PotDev& p, int off);
-template <> __device__ __forceinline__ double pot_tab<double>(const PotDev& p, int off) { return p.tab64[off]; }
-template <> __device__ __forceinline__ float pot_tab<float>(const PotDev& p, int off) { return p.tab32[off]; }
+template <typename T> __device__ __forceinline__ T pot_tab(const PotDev& p, long long off);
+template <> __device__ __forceinline__ double pot_tab<double>(const PotDev& p, long long off) { return p.tab64[off]; }
+template <> __device__ __forceinline__ float pot_tab<float>(const PotDev& p, long long off) { return p.tab32[off]; }
 template <typename T> __device__ __forceinline__ T pot_grid(const PotDev& p, long long i);
 template <> __device__ __forceinline__ double pot_grid<double>(const PotDev& p, long long i) { return p.grid64[i]; }
 template <> __device__ __forceinline__ float pot_grid<float>(const PotDev& p, long long i) { return p.grid32[i]; }
@@ -146,6 +147,11 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
   const long long c0 = (tile_id % a.tiles_inner) * a.C;
   const int Ot = (int)min((long long)a.Ot, a.outer - o0);
   const int vec = blockIdx.y;
+  int prob = 0;
+  if (a.pot.vecs_per_prob > 0) {
+    prob = (a.vec_base + vec) / a.pot.vecs_per_prob;
+    if (a.pot.active && !a.pot.active[prob]) return;
+  }
   const V2* in = reinterpret_cast<const V2*>(a.in) + (size_t)vec * a.ld;
   V2* out = reinterpret_cast<V2*>(a.out) + (size_t)vec * a.ld;
 
@@ -175,6 +181,7 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
       __syncthreads();
     }
     // multiply by V(y_l)/N: l_II from the group point, l_I from the inner index
+    const long long tbase = (long long)prob * a.pot.tab_stride;
     for (int e = threadIdx.x; e < nel; e += blockDim.x) {
       const int c = e % C;
       const int g = (e / C) % M;
@@ -185,13 +192,13 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
         for (int j = a.g.d - 1; j >= 0; --j) {
           const int lj = (int)(rem % a.g.lens[j]);
           rem /= a.g.lens[j];
-          v += pot_tab<T>(a.pot, a.pot.tab_off[j] + lj);
+          v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[j] + lj);
         }
         int gr = g;                          // group point -> l_II coordinates
         for (int ax = a.grp.ng - 1; ax >= 0; --ax) {
           const int lj = gr % a.grp.len[ax];
           gr /= a.grp.len[ax];
-          v += pot_tab<T>(a.pot, a.pot.tab_off[a.g.d + ax] + lj);
+          v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[a.g.d + ax] + lj);
         }
       } else {
         v = pot_grid<T>(a.pot, (long long)g * a.inner + c0 + c);
@@ -318,7 +325,8 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
 
 template <typename T>
 iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaStream_t stream,
-                       PassTimer* timer, void* ext_work = nullptr, size_t ext_bytes = 0) {
+                       PassTimer* timer, void* ext_work = nullptr, size_t ext_bytes = 0,
+                       const ApplyBatch* batch = nullptr) {
   using V2 = typename Vec2<T>::type;
   const Geom& g = p->g;
   const int d = g.d, n = g.n;
@@ -345,9 +353,20 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
   pot.grid64 = p->d_grid64; pot.grid32 = p->d_grid32;
   pot.c64 = p->vconst / (double)g.N;
   pot.c32 = (float)pot.c64;
+  if (batch) {
+    // batch tables: axis j's table follows axes 0..j-1 (lens[0] + ... + lens[j-1])
+    int off = 0;
+    for (int j = 0; j < n; ++j) { pot.tab_off[j] = off; off += g.lens[j]; }
+    pot.kind = 1;
+    pot.tab64 = batch->tab64; pot.tab32 = batch->tab32;
+    pot.c64 = 0.0; pot.c32 = 0.f;             // folded into the tables
+    pot.tab_stride = batch->tab_stride;
+    pot.vecs_per_prob = batch->vecs_per_prob;
+    pot.active = batch->active;
+  }
 
   PassArgs A{};
-  A.g = g; A.lo = p->d_lo; A.ld = g.N;
+  A.g = g; A.lo = p->d_lo; A.ld = g.N; A.pot = pot;
   A.grp.ng = d; A.M = (int)g.MI; A.inner = 1; A.outer = g.MII;
   for (int j = 0; j < d; ++j) { A.grp.len[j] = g.lens[j]; A.grp.kI[j] = j; A.grp.Lroll[j] = 0; }
   {
@@ -376,6 +395,7 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     const V2* in = reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N;
     V2* out = reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N;
     V2* wk = reinterpret_cast<V2*>(work);
+    A.vec_base = v0; B.vec_base = v0; Cp.vec_base = v0;
     A.in = in; A.out = wk;
     IWF_TRY((launch_pass<T, 0>(A, nv, stream, timer)));
     B.in = wk; B.out = wk;
@@ -395,17 +415,19 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
-                      cudaStream_t stream, PassTimer* timer) {
+                      cudaStream_t stream, PassTimer* timer, const ApplyBatch* batch) {
   if (nvec < 0) return fail(IWF_ERR_ARG, "iwf_apply: nvec < 0");
   if (nvec == 0) return IWF_OK;
   if (!psi || !hpsi) return fail(IWF_ERR_ARG, "iwf_apply: null vector pointer");
   if ((reinterpret_cast<uintptr_t>(psi) | reinterpret_cast<uintptr_t>(hpsi)) & 15)
     return fail(IWF_ERR_ARG, "iwf_apply: vectors must be 16-byte aligned");
-  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_apply: no potential set");
+  if (p->pot_kind == 0 && !batch) return fail(IWF_ERR_ARG, "iwf_apply: no potential set");
   if (nvec > 65535) return fail(IWF_ERR_ARG, "iwf_apply: nvec > 65535");
   IWF_TRY(init_twiddles(p->device));
-  if (precision == IWF_PREC_F64) return apply_typed<double>(p, psi, hpsi, nvec, stream, timer);
-  if (precision == IWF_PREC_C64) return apply_typed<float>(p, psi, hpsi, nvec, stream, timer);
+  if (precision == IWF_PREC_F64)
+    return apply_typed<double>(p, psi, hpsi, nvec, stream, timer, nullptr, 0, batch);
+  if (precision == IWF_PREC_C64)
+    return apply_typed<float>(p, psi, hpsi, nvec, stream, timer, nullptr, 0, batch);
   return fail(IWF_ERR_ARG, "iwf_apply: unknown precision");
 }
 

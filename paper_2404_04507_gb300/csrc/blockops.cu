@@ -1,4 +1,5 @@
 // Block kernels of the eigensolver (declarations and layout conventions in blockops.cuh).
+#include <algorithm>
 #include <cmath>
 
 #include "blockops.cuh"
@@ -19,9 +20,14 @@ template <> struct Acc<float> { using type = float; };
 // launch picks U = ceil(ma/24), V = ceil(mb/24) and no thread multiplies padding.
 template <typename T, int U, int V>
 __global__ void __launch_bounds__(kGramThreads)
-gram_kernel(BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
+gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const size_t poff = (size_t)prob * bt.pstride;
+  for (int i = 0; i < A.nb; ++i) A.p[i] = reinterpret_cast<const V2*>(A.p[i]) + poff;
+  for (int i = 0; i < B.nb; ++i) B.p[i] = reinterpret_cast<const V2*>(B.p[i]) + poff;
   __shared__ V2 sa[kGramRows][kMaxSmall + 1];
   __shared__ V2 sb[kGramRows][kMaxSmall + 1];
   const int tx = threadIdx.x % kGramTx, ty = threadIdx.x / kGramTx;
@@ -74,7 +80,7 @@ gram_kernel(BlockList A, BlockList B, int ma, int mb, long long N, double2* part
       for (int v = 0; v < V; ++v) { sumr[u][v] += (double)accr[u][v]; sumi[u][v] += (double)acci[u][v]; }
     __syncthreads();
   }
-  double2* out = partial + (size_t)blockIdx.x * ma * mb;
+  double2* out = partial + ((size_t)prob * gridDim.x + blockIdx.x) * ma * mb;
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -84,16 +90,20 @@ gram_kernel(BlockList A, BlockList B, int ma, int mb, long long N, double2* part
     }
 }
 
-// Sum the per-CTA partials in a fixed order (deterministic).
-__global__ void reduce_partials(const double2* partial, int slots, int count, double2* out) {
+// Sum the per-CTA partials in a fixed order (deterministic); problem blockIdx.y.
+__global__ void reduce_partials(Batch bt, const double2* partial, int slots, int count,
+                                double2* out) {
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= count) return;
+  const double2* pp = partial + (size_t)prob * slots * count;
   double re = 0, im = 0;
   for (int s = 0; s < slots; ++s) {
-    const double2 v = partial[(size_t)s * count + e];
+    const double2 v = pp[(size_t)s * count + e];
     re += v.x; im += v.y;
   }
-  out[e] = make_double2(re, im);
+  out[(size_t)prob * kCapG + e] = make_double2(re, im);
 }
 
 constexpr int kUpdRows = 16;
@@ -102,10 +112,18 @@ constexpr int kUpdThreads = kUpdRows * kMaxBlock;
 // out1[:, j] (=|-=) sum_k S[:, k] C1[k, j]; out2 likewise with C2. C row-major m x q.
 template <typename T, bool SUB>
 __global__ void __launch_bounds__(kUpdThreads)
-update_kernel(BlockList S, int m, long long N, const double2* C1, const double2* C2, int q,
-              typename Cplx<T>::type* out1, typename Cplx<T>::type* out2) {
+update_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, const double2* C2,
+              int cstride, int q, typename Cplx<T>::type* out1, typename Cplx<T>::type* out2) {
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const size_t poff = (size_t)prob * bt.pstride;
+  for (int i = 0; i < S.nb; ++i) S.p[i] = reinterpret_cast<const V2*>(S.p[i]) + poff;
+  out1 += poff;
+  if (out2) out2 += poff;
+  C1 += (size_t)prob * cstride;
+  if (C2) C2 += (size_t)prob * cstride;
   extern __shared__ __align__(16) unsigned char upd_raw[];
   double2* sc1 = reinterpret_cast<double2*>(upd_raw);
   double2* sc2 = sc1 + kMaxSmall * kMaxBlock;
@@ -162,18 +180,25 @@ constexpr int kResThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kResThreads)
-residual_kernel(const typename Cplx<T>::type* X, const typename Cplx<T>::type* HX,
-                const double* theta, const T* M, typename Cplx<T>::type* W, long long N, int b,
-                double* partial) {
+residual_kernel(Batch bt, const typename Cplx<T>::type* X, const typename Cplx<T>::type* HX,
+                const double* theta, const double* lam, const double* shift, const double* off2,
+                typename Cplx<T>::type* W, long long N, int b, double* partial) {
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const size_t poff = (size_t)prob * bt.pstride;
+  X += poff; HX += poff; W += poff;
+  theta += (size_t)prob * kMaxBlock;
+  const double sh = shift[prob], o2 = off2[prob];
   __shared__ double red[kResThreads / 32][kMaxBlock];  // b <= kMaxBlock
   AT acc[kMaxBlock];
 #pragma unroll
   for (int j = 0; j < kMaxBlock; ++j) acc[j] = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    const T mi = M[i];
+    const double h = lam[i] + sh;
+    const T mi = (T)(h / (h * h + o2));
 #pragma unroll
     for (int j = 0; j < kMaxBlock; ++j) {
       if (j >= b) break;
@@ -198,16 +223,18 @@ residual_kernel(const typename Cplx<T>::type* X, const typename Cplx<T>::type* H
   if (threadIdx.x < b) {
     double v = 0;
     for (int w = 0; w < kResThreads / 32; ++w) v += red[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * b + threadIdx.x] = v;
+    partial[((size_t)prob * gridDim.x + blockIdx.x) * b + threadIdx.x] = v;
   }
 }
 
-__global__ void resid_finish(const double* partial, int slots, int b, double* resid) {
+__global__ void resid_finish(Batch bt, const double* partial, int slots, int b, double* resid) {
+  const int prob = blockIdx.x;
+  if (bt.active && !bt.active[prob]) return;
   const int j = threadIdx.x;
   if (j >= b) return;
   double s = 0;
-  for (int c = 0; c < slots; ++c) s += partial[(size_t)c * b + j];
-  resid[j] = sqrt(s);
+  for (int c = 0; c < slots; ++c) s += partial[((size_t)prob * slots + c) * b + j];
+  resid[(size_t)prob * kMaxBlock + j] = sqrt(s);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -382,10 +409,16 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
 // D = diag(G)^{-1/2}, D G D = U S U^H, T = D U S^{-1/2} restricted to S > drop * max(S).
 // Columns of T beyond the kept rank are zero and their mask entry is 0.
 __global__ void __launch_bounds__(kSmallThreads)
-svqb_kernel(const double2* G, int b, double drop, double2* T, int* mask, int* status) {
+svqb_kernel(Batch bt, const double2* G, int b, double drop, double2* T, int* mask, int* status) {
   extern __shared__ __align__(16) unsigned char raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(raw);
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int prob = blockIdx.x;
+  if (bt.active && !bt.active[prob]) return;
+  G += (size_t)prob * kCapG;
+  T += (size_t)prob * kCapT;
+  mask += (size_t)prob * kMaxBlock;
+  if (status) status += prob;
   for (int i = tid; i < b; i += nt) {
     const double g = G[i * b + i].x;
     sh.w[i] = g > 1e-300 ? 1.0 / sqrt(g) : 0.0;
@@ -427,11 +460,20 @@ svqb_kernel(const double2* G, int b, double drop, double2* T, int* mask, int* st
 // and orthonormalised in the coefficient space, so that S Cp is orthonormal and orthogonal
 // to S Cx; dependent columns are zero with mask_p = 0.
 __global__ void __launch_bounds__(kSmallThreads)
-rr_kernel(const double2* Ain, int m, int b, const int* mask, int x_rows, double* theta,
-          double2* Cx, double2* Cp, int* mask_p, int* status) {
+rr_kernel(Batch bt, const double2* Ain, int m, int b, const int* mask, int x_rows,
+          double* theta, double2* Cx, double2* Cp, int* mask_p, int* status) {
   extern __shared__ __align__(16) unsigned char raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(raw);
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int prob = blockIdx.x;
+  if (bt.active && !bt.active[prob]) return;
+  Ain += (size_t)prob * kCapG;
+  mask += (size_t)prob * kMaxSmall;
+  theta += (size_t)prob * kMaxBlock;
+  Cx += (size_t)prob * kCapC;
+  Cp += (size_t)prob * kCapC;
+  mask_p += (size_t)prob * kMaxBlock;
+  status += prob;
   if (tid == 0) {
     int na = 0;
     for (int i = 0; i < m; ++i) if (mask[i]) sh.idx[na++] = i;
@@ -540,14 +582,6 @@ rr_kernel(const double2* Ain, int m, int b, const int* mask, int x_rows, double*
   if (tid == 0) *status = 0;
 }
 
-template <typename T>
-__global__ void precond_kernel(const double* lam, double shift, double off2, long long N, T* M) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const double h = lam[i] + shift;
-  M[i] = (T)(h / (h * h + off2));
-}
-
 template <typename Tin, typename Tout>
 __global__ void convert_kernel(const Tin* in, Tout* out, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
@@ -576,8 +610,11 @@ __global__ void random_kernel(typename Cplx<T>::type* X, long long count, unsign
   }
 }
 
-__global__ void mask_kernel(int* mask, int b, int value) {
-  if ((int)threadIdx.x < b) mask[threadIdx.x] = value;
+__global__ void mask_kernel(int nprob, int* mask, int off, int b, int value, const int* src) {
+  const int prob = blockIdx.x;
+  const int j = threadIdx.x;
+  if (prob >= nprob || j >= b) return;
+  mask[(size_t)prob * kMaxSmall + off + j] = src ? src[(size_t)prob * kMaxBlock + j] : value;
 }
 
 int grid_for(long long work, int per_block) {
@@ -590,16 +627,17 @@ int grid_for(long long work, int per_block) {
 }  // namespace
 
 template <typename T>
-iwf_status gram(const BlockList& A, const BlockList& B, long long N, double2* out,
-                double2* partial, int partial_slots, cudaStream_t s) {
+iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long long N, double2* out,
+                double2* partial, int slots_per_prob, cudaStream_t s) {
   const int ma = A.nb * A.b, mb = B.nb * B.b;
   if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram: too many columns");
   int g = grid_for(N, kGramRows);
-  if (g > partial_slots) g = partial_slots;
+  if (g > slots_per_prob) g = slots_per_prob;
   const int U = (ma + kGramTx - 1) / kGramTx, V = (mb + kGramTx - 1) / kGramTx;
+  const dim3 grid(g, bt.nprob);
   switch (U * 4 + V) {
 #define IWF_GRAM(U_, V_) \
-    case U_ * 4 + V_: gram_kernel<T, U_, V_><<<g, kGramThreads, 0, s>>>(A, B, ma, mb, N, partial); break;
+    case U_ * 4 + V_: gram_kernel<T, U_, V_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); break;
     IWF_GRAM(1, 1) IWF_GRAM(1, 2) IWF_GRAM(1, 3) IWF_GRAM(2, 1) IWF_GRAM(2, 2) IWF_GRAM(2, 3)
     IWF_GRAM(3, 1) IWF_GRAM(3, 2) IWF_GRAM(3, 3)
 #undef IWF_GRAM
@@ -608,20 +646,24 @@ iwf_status gram(const BlockList& A, const BlockList& B, long long N, double2* ou
   IWF_CUDA(cudaGetLastError());
   count_launch();
   const int cnt = ma * mb;
-  reduce_partials<<<(cnt + 255) / 256, 256, 0, s>>>(partial, g, cnt, out);
+  reduce_partials<<<dim3((cnt + 255) / 256, bt.nprob), 256, 0, s>>>(bt, partial, g, cnt, out);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
 }
 
 template <typename T>
-iwf_status block_update(const BlockList& S, long long N, const double2* C1, const double2* C2,
-                        int q, void* out1, void* out2, bool subtract, cudaStream_t s) {
+iwf_status block_update(const Batch& bt, const BlockList& S, long long N, const double2* C1,
+                        const double2* C2, int cstride, int q, void* out1, void* out2,
+                        bool subtract, cudaStream_t s) {
   // (the static attribute flags below are per instantiation of T)
   using V2 = typename Cplx<T>::type;
   const int m = S.nb * S.b;
   if (m > kMaxSmall || q > kMaxBlock || q < 1) return fail(IWF_ERR_ARG, "block_update: shape");
-  const int g = grid_for(N, kUpdRows);
+  if (cstride < m * q) return fail(IWF_ERR_ARG, "block_update: coefficient stride too small");
+  int g0 = grid_for(N, kUpdRows);
+  if (bt.nprob > 1) g0 = std::max(1, std::min(g0, (8 * 152 + bt.nprob - 1) / bt.nprob));
+  const dim3 g(g0, bt.nprob);
   const size_t dyn = 2 * sizeof(double2) * kMaxSmall * kMaxBlock;
   static bool attr[2] = {false, false};
   if (!attr[subtract]) {
@@ -634,10 +676,10 @@ iwf_status block_update(const BlockList& S, long long N, const double2* C1, cons
     attr[subtract] = true;
   }
   if (subtract)
-    update_kernel<T, true><<<g, kUpdThreads, dyn, s>>>(S, m, N, C1, nullptr, q,
+    update_kernel<T, true><<<g, kUpdThreads, dyn, s>>>(bt, S, m, N, C1, nullptr, cstride, q,
                                                        reinterpret_cast<V2*>(out1), nullptr);
   else
-    update_kernel<T, false><<<g, kUpdThreads, dyn, s>>>(S, m, N, C1, C2, q,
+    update_kernel<T, false><<<g, kUpdThreads, dyn, s>>>(bt, S, m, N, C1, C2, cstride, q,
                                                         reinterpret_cast<V2*>(out1),
                                                         reinterpret_cast<V2*>(out2));
   IWF_CUDA(cudaGetLastError());
@@ -646,18 +688,19 @@ iwf_status block_update(const BlockList& S, long long N, const double2* C1, cons
 }
 
 template <typename T>
-iwf_status residual_precond(const void* X, const void* HX, const double* theta, const T* M,
-                            void* W, long long N, int b, double* partial, int partial_slots,
+iwf_status residual_precond(const Batch& bt, const void* X, const void* HX, const double* theta,
+                            const double* lam, const double* shift, const double* off2,
+                            void* W, long long N, int b, double* partial, int slots_per_prob,
                             double* resid, cudaStream_t s) {
   using V2 = typename Cplx<T>::type;
   int g = grid_for(N, kResThreads);
-  if (g > partial_slots) g = partial_slots;
-  residual_kernel<T><<<g, kResThreads, 0, s>>>(reinterpret_cast<const V2*>(X),
-                                               reinterpret_cast<const V2*>(HX), theta, M,
-                                               reinterpret_cast<V2*>(W), N, b, partial);
+  if (g > slots_per_prob) g = slots_per_prob;
+  residual_kernel<T><<<dim3(g, bt.nprob), kResThreads, 0, s>>>(
+      bt, reinterpret_cast<const V2*>(X), reinterpret_cast<const V2*>(HX), theta, lam, shift,
+      off2, reinterpret_cast<V2*>(W), N, b, partial);
   IWF_CUDA(cudaGetLastError());
   count_launch();
-  resid_finish<<<1, 32, 0, s>>>(partial, g, b, resid);
+  resid_finish<<<bt.nprob, 32, 0, s>>>(bt, partial, g, b, resid);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
@@ -669,32 +712,23 @@ static iwf_status small_smem_attr(const void* fn) {
   return IWF_OK;
 }
 
-iwf_status svqb_small(const double2* G, int b, double drop, double2* T, int* mask, int* status,
-                      cudaStream_t s) {
+iwf_status svqb_small(const Batch& bt, const double2* G, int b, double drop, double2* T,
+                      int* mask, int* status, cudaStream_t s) {
   static bool attr = false;
   if (!attr) { IWF_TRY(small_smem_attr((const void*)svqb_kernel)); attr = true; }
-  svqb_kernel<<<1, kSmallThreads, sizeof(SmallShared), s>>>(G, b, drop, T, mask, status);
+  svqb_kernel<<<bt.nprob, kSmallThreads, sizeof(SmallShared), s>>>(bt, G, b, drop, T, mask, status);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
 }
 
-iwf_status rayleigh_ritz_small(const double2* A, int m, int b, const int* mask, int x_rows,
-                               double* theta, double2* Cx, double2* Cp, int* mask_p,
-                               int* status, cudaStream_t s) {
+iwf_status rayleigh_ritz_small(const Batch& bt, const double2* A, int m, int b, const int* mask,
+                               int x_rows, double* theta, double2* Cx, double2* Cp,
+                               int* mask_p, int* status, cudaStream_t s) {
   static bool attr = false;
   if (!attr) { IWF_TRY(small_smem_attr((const void*)rr_kernel)); attr = true; }
-  rr_kernel<<<1, kSmallThreads, sizeof(SmallShared), s>>>(A, m, b, mask, x_rows, theta, Cx, Cp,
-                                                          mask_p, status);
-  IWF_CUDA(cudaGetLastError());
-  count_launch();
-  return IWF_OK;
-}
-
-template <typename T>
-iwf_status precond_diag(const double* lam, double shift, double off2, long long N, T* M,
-                        cudaStream_t s) {
-  precond_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(lam, shift, off2, N, M);
+  rr_kernel<<<bt.nprob, kSmallThreads, sizeof(SmallShared), s>>>(bt, A, m, b, mask, x_rows, theta,
+                                                                 Cx, Cp, mask_p, status);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
@@ -719,31 +753,30 @@ iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cu
   return IWF_OK;
 }
 
-iwf_status set_mask(int* mask, int b, int value, cudaStream_t s) {
-  mask_kernel<<<1, 64, 0, s>>>(mask, b, value);
+iwf_status set_mask(const Batch& bt, int* mask, int off, int b, int value, const int* src,
+                    cudaStream_t s) {
+  mask_kernel<<<bt.nprob, 32, 0, s>>>(bt.nprob, mask, off, b, value, src);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
 }
 
-template iwf_status gram<double>(const BlockList&, const BlockList&, long long, double2*,
-                                 double2*, int, cudaStream_t);
-template iwf_status gram<float>(const BlockList&, const BlockList&, long long, double2*,
-                                double2*, int, cudaStream_t);
-template iwf_status block_update<double>(const BlockList&, long long, const double2*,
-                                         const double2*, int, void*, void*, bool, cudaStream_t);
-template iwf_status block_update<float>(const BlockList&, long long, const double2*,
-                                        const double2*, int, void*, void*, bool, cudaStream_t);
-template iwf_status residual_precond<double>(const void*, const void*, const double*,
-                                             const double*, void*, long long, int, double*, int,
-                                             double*, cudaStream_t);
-template iwf_status residual_precond<float>(const void*, const void*, const double*,
-                                            const float*, void*, long long, int, double*, int,
-                                            double*, cudaStream_t);
-template iwf_status precond_diag<double>(const double*, double, double, long long, double*,
+template iwf_status gram<double>(const Batch&, const BlockList&, const BlockList&, long long,
+                                 double2*, double2*, int, cudaStream_t);
+template iwf_status gram<float>(const Batch&, const BlockList&, const BlockList&, long long,
+                                double2*, double2*, int, cudaStream_t);
+template iwf_status block_update<double>(const Batch&, const BlockList&, long long, const double2*,
+                                         const double2*, int, int, void*, void*, bool,
                                          cudaStream_t);
-template iwf_status precond_diag<float>(const double*, double, double, long long, float*,
+template iwf_status block_update<float>(const Batch&, const BlockList&, long long, const double2*,
+                                        const double2*, int, int, void*, void*, bool,
                                         cudaStream_t);
+template iwf_status residual_precond<double>(const Batch&, const void*, const void*, const double*,
+                                             const double*, const double*, const double*, void*,
+                                             long long, int, double*, int, double*, cudaStream_t);
+template iwf_status residual_precond<float>(const Batch&, const void*, const void*, const double*,
+                                            const double*, const double*, const double*, void*,
+                                            long long, int, double*, int, double*, cudaStream_t);
 template iwf_status convert_block<double, float>(const void*, void*, long long, cudaStream_t);
 template iwf_status convert_block<float, double>(const void*, void*, long long, cudaStream_t);
 template iwf_status random_block<double>(void*, long long, int, unsigned long long, cudaStream_t);

@@ -34,31 +34,49 @@ __device__ __forceinline__ const typename Cplx<T>::type* col_ptr(const BlockList
   return reinterpret_cast<const V2*>(L.p[k / L.b]) + (size_t)(k % L.b) * N;
 }
 
+// A batch of nprob independent problems with the same geometry. Problem p's long blocks
+// start pstride elements after problem p-1's (every BlockList pointer is problem 0's).
+// Small per-problem matrices sit at fixed capacities: G kMaxSmall^2, C kMaxSmall*kMaxBlock,
+// T kMaxBlock^2, theta/resid kMaxBlock, masks kMaxSmall. active (may be null): problems
+// with active[p] == 0 are skipped by every kernel.
+struct Batch {
+  int nprob;
+  long long pstride;
+  const int* active;
+};
+constexpr int kCapG = kMaxSmall * kMaxSmall;
+constexpr int kCapC = kMaxSmall * kMaxBlock;
+constexpr int kCapT = kMaxBlock * kMaxBlock;
+
 // Host-side launchers (defined in blockops.cu).
 template <typename T>
-iwf_status gram(const BlockList& A, const BlockList& B, long long N, double2* out,
-                double2* partial, int partial_slots, cudaStream_t s);
+iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long long N, double2* out,
+                double2* partial, int slots_per_prob, cudaStream_t s);
 // out = S C1 (and out2 = S C2 when C2 != nullptr); subtract: out -= S C1 instead.
+// Problem p's coefficient matrices start at C1 + p*cstride (kCapG for Gram outputs,
+// kCapT for SVQB transforms, kCapC for Rayleigh-Ritz coefficients).
 template <typename T>
-iwf_status block_update(const BlockList& S, long long N, const double2* C1, const double2* C2,
-                        int q, void* out1, void* out2, bool subtract, cudaStream_t s);
-// R = HX - X diag(theta); W = M R; partial squared column norms of R -> resid (sqrt'ed).
+iwf_status block_update(const Batch& bt, const BlockList& S, long long N, const double2* C1,
+                        const double2* C2, int cstride, int q, void* out1, void* out2,
+                        bool subtract, cudaStream_t s);
+// R = HX - X diag(theta); W = M R with M_k = h/(h^2 + off2[p]), h = lam_k + shift[p]
+// (Eq. precond, shifted); squared column norms of R -> resid (sqrt'ed).
 template <typename T>
-iwf_status residual_precond(const void* X, const void* HX, const double* theta, const T* M,
-                            void* W, long long N, int b, double* partial, int partial_slots,
+iwf_status residual_precond(const Batch& bt, const void* X, const void* HX, const double* theta,
+                            const double* lam, const double* shift, const double* off2,
+                            void* W, long long N, int b, double* partial, int slots_per_prob,
                             double* resid, cudaStream_t s);
-iwf_status svqb_small(const double2* G, int b, double drop, double2* T, int* mask,
-                      int* status, cudaStream_t s);
-iwf_status rayleigh_ritz_small(const double2* A, int m, int b, const int* mask, int x_rows,
-                               double* theta, double2* Cx, double2* Cp, int* mask_p,
-                               int* status, cudaStream_t s);
-template <typename T>
-iwf_status precond_diag(const double* lam, double shift, double off2, long long N, T* M,
-                        cudaStream_t s);
+iwf_status svqb_small(const Batch& bt, const double2* G, int b, double drop, double2* T,
+                      int* mask, int* status, cudaStream_t s);
+iwf_status rayleigh_ritz_small(const Batch& bt, const double2* A, int m, int b, const int* mask,
+                               int x_rows, double* theta, double2* Cx, double2* Cp,
+                               int* mask_p, int* status, cudaStream_t s);
 template <typename Tin, typename Tout>
 iwf_status convert_block(const void* in, void* out, long long count, cudaStream_t s);
 template <typename T>
 iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cudaStream_t s);
-iwf_status set_mask(int* mask, int b, int value, cudaStream_t s);
+// mask[p*kMaxSmall + off + j] = value (or src[p*kMaxBlock + j]) for j < b, every problem.
+iwf_status set_mask(const Batch& bt, int* mask, int off, int b, int value, const int* src,
+                    cudaStream_t s);
 
 }  // namespace iwf

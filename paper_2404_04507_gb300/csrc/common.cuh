@@ -66,6 +66,19 @@ struct PotDev {
   float c32;
   const double* grid64;    // kind 2: N values, data layout (l_II slow, l_I fast)
   const float* grid32;
+  long long tab_stride;    // batches: table entries between consecutive problems
+  int vecs_per_prob;       // batches: vectors per problem (0: one problem)
+  const int* active;       // batches: problem p skipped when active[p] == 0 (may be null)
+};
+
+// Per-problem potential tables of a batch of problems sharing one plan's geometry: problem
+// p's axis tables (constant term folded into axis 0) start at p * tab_stride.
+struct ApplyBatch {
+  const double* tab64;
+  const float* tab32;
+  long long tab_stride;
+  int vecs_per_prob;
+  const int* active;
 };
 
 }  // namespace iwf
@@ -106,15 +119,31 @@ struct PassTimer {
   int launches[3] = {0, 0, 0};
 };
 iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
-                      cudaStream_t stream, PassTimer* timer = nullptr);
+                      cudaStream_t stream, PassTimer* timer = nullptr,
+                      const ApplyBatch* batch = nullptr);
 iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                               cudaStream_t stream);
 iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
                            void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st);
+iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, const int* m,
+                                 const double* re, const double* im, const iwf_solve_opts* o,
+                                 double* evals, void* evecs, double* resid, int* iters,
+                                 iwf_solve_info* info, cudaStream_t st);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties
 iwf_status export_window(const iwf_plan* p, int* k_host);
 iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
                            const double* im);
+// Potential summaries used by the preconditioner (Eq. precond): Re Vg_0, sum |Vg_m|,
+// sum |Vg_m|^2 over m != 0 after folding onto the grid.
+struct PotSummary {
+  double vg0 = 0, off_abs = 0, off_sq = 0;
+  bool separable = true;
+};
+// Per-axis tables (scaled by 1/N, constant folded into axis 0) of one separable potential,
+// written at tab64/tab32 (length sum of lens); the host summary goes to *sum.
+iwf_status potential_tables(const iwf_plan* p, int nmodes, const int* m, const double* re,
+                            const double* im, double* tab64, float* tab32, PotSummary* sum,
+                            cudaStream_t s);
 }  // namespace iwf

@@ -1,21 +1,26 @@
-// Block LOBPCG for the lowest eigenpairs of H~ (Sec. 4.1, Alg. 2 in block form).
+// Block LOBPCG for the lowest eigenpairs of H~ (Sec. 4.1, Alg. 2 in block form), for one
+// problem or a batch of problems sharing one plan's geometry (different potentials).
 //
-// Every iteration keeps an orthonormal basis S = [X W P] of the trial subspace:
+// Every iteration keeps an orthonormal basis S = [X W P] of each problem's trial subspace:
 //   R = H X - X diag(theta), W = M R            (preconditioner of Eq. precond, shifted)
 //   W <- W - [X P]([X P]^H W), twice            (classical Gram-Schmidt, reorthogonalised)
 //   W <- W D U S^{-1/2}, twice                   (SVQB; dependent directions dropped)
 //   HW = H W                                      (the FFT apply)
-//   A = S^H [HX HW HP]; A = Y diag(theta) Y^H     (one-CTA Jacobi, FP64)
-//   X <- S Yx, P <- S Yp with Yp orthonormalised against Yx in the small space, so that
-//   [X P] stays orthonormal without touching the long vectors again.
+//   A = S^H [HX HW HP]; A = Y diag(theta) Y^H     (one-CTA Jacobi per problem, FP64)
+//   X <- S Yx, P <- S Yp with Yp orthonormalised against Yx in the coefficient space, so
+//   that [X P] stays orthonormal without touching the long vectors again.
+// All problems advance in lockstep through the same kernels (problem index in the grid);
+// converged problems are switched off by a device flag every kernel reads. The steady-state
+// iteration is captured once into two CUDA graphs (the buffer sets alternate) and replayed;
+// the host reads only the residual norms after each replay.
 // Mixed precision: a first phase stores the blocks in complex float and applies H in
 // complex float (Gram sums in float within 16-row tiles, double across tiles); its X then
 // seeds the FP64 phase, which runs to the requested tolerance.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <cmath>
 #include <vector>
 
 #include "blockops.cuh"
@@ -34,23 +39,12 @@ int log_level() {
   return level;
 }
 
-template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? IWF_PREC_F64 : IWF_PREC_C64; }
+bool graphs_enabled() {
+  static const bool on = [] { return std::getenv("IWF_NO_GRAPH") == nullptr; }();
+  return on;
+}
 
-struct SmallBufs {
-  double2* G = nullptr;       // kMaxSmall^2
-  double2* Cx = nullptr;      // kMaxSmall x kMaxBlock
-  double2* Cp = nullptr;
-  double2* T = nullptr;       // kMaxBlock^2
-  double* theta = nullptr;    // kMaxBlock
-  double* resid = nullptr;    // kMaxBlock
-  int* mask = nullptr;        // kMaxSmall (X | W | P)
-  int* maskw = nullptr;       // kMaxBlock
-  int* maskp = nullptr;       // kMaxBlock
-  int* status = nullptr;
-  double2* partial = nullptr; // slots x kMaxSmall^2
-  double* rpartial = nullptr; // slots x kMaxBlock
-  int slots = 608;
-};
+template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? IWF_PREC_F64 : IWF_PREC_C64; }
 
 struct Arena {
   std::vector<void*> ptrs;
@@ -66,27 +60,43 @@ struct Arena {
   }
 };
 
-iwf_status alloc_small(Arena& ar, SmallBufs& s) {
-  IWF_TRY(ar.get(&s.G, kMaxSmall * kMaxSmall));
-  IWF_TRY(ar.get(&s.Cx, kMaxSmall * kMaxBlock));
-  IWF_TRY(ar.get(&s.Cp, kMaxSmall * kMaxBlock));
-  IWF_TRY(ar.get(&s.T, kMaxBlock * kMaxBlock));
-  IWF_TRY(ar.get(&s.theta, kMaxBlock));
-  IWF_TRY(ar.get(&s.resid, kMaxBlock));
-  IWF_TRY(ar.get(&s.mask, kMaxSmall));
-  IWF_TRY(ar.get(&s.maskw, kMaxBlock));
-  IWF_TRY(ar.get(&s.maskp, kMaxBlock));
-  IWF_TRY(ar.get(&s.status, 1));
-  IWF_TRY(ar.get(&s.partial, (size_t)s.slots * kMaxSmall * kMaxSmall));
-  IWF_TRY(ar.get(&s.rpartial, (size_t)s.slots * kMaxBlock));
+// Per-problem small buffers (fixed capacities, see blockops.cuh) and problem parameters.
+struct Small {
+  int nprob = 1;
+  int slots = 608;             // Gram / residual partial slots per problem
+  double2 *G, *Cx, *Cp, *T, *partial;
+  double *theta, *resid, *rpartial;
+  int *mask, *maskw, *maskp, *status, *active;
+  double *shift, *off2;        // preconditioner parameters per problem
+};
+
+iwf_status alloc_small(Arena& ar, Small& s, int nprob) {
+  s.nprob = nprob;
+  s.slots = std::max(8, std::min(608, (4 * 608) / nprob));
+  IWF_TRY(ar.get(&s.G, (size_t)nprob * kCapG));
+  IWF_TRY(ar.get(&s.Cx, (size_t)nprob * kCapC));
+  IWF_TRY(ar.get(&s.Cp, (size_t)nprob * kCapC));
+  IWF_TRY(ar.get(&s.T, (size_t)nprob * kCapT));
+  IWF_TRY(ar.get(&s.theta, (size_t)nprob * kMaxBlock));
+  IWF_TRY(ar.get(&s.resid, (size_t)nprob * kMaxBlock));
+  IWF_TRY(ar.get(&s.mask, (size_t)nprob * kMaxSmall));
+  IWF_TRY(ar.get(&s.maskw, (size_t)nprob * kMaxBlock));
+  IWF_TRY(ar.get(&s.maskp, (size_t)nprob * kMaxBlock));
+  IWF_TRY(ar.get(&s.status, (size_t)nprob));
+  IWF_TRY(ar.get(&s.active, (size_t)nprob));
+  IWF_TRY(ar.get(&s.shift, (size_t)nprob));
+  IWF_TRY(ar.get(&s.off2, (size_t)nprob));
+  IWF_TRY(ar.get(&s.partial, (size_t)nprob * s.slots * kCapG));
+  IWF_TRY(ar.get(&s.rpartial, (size_t)nprob * s.slots * kMaxBlock));
   return IWF_OK;
 }
 
 struct PhaseResult {
-  int iters = 0;
+  std::vector<int> iters;        // per problem: iterations until it converged (or stopped)
+  std::vector<int> converged;
   long long applies = 0;
-  bool converged = false;
-  std::vector<double> theta, resid;
+  int rounds = 0;                // lockstep iterations of the phase
+  std::vector<double> theta, resid;  // nprob x kMaxBlock
 };
 
 BlockList blocks(std::initializer_list<const void*> ps, int b) {
@@ -98,192 +108,358 @@ BlockList blocks(std::initializer_list<const void*> ps, int b) {
   return L;
 }
 
-// One LOBPCG phase with blocks stored as T. X (N x b) is the start block (overwritten by
-// the result); stops when the first nev residuals are <= tol, after maxit iterations, or
-// (when stall > 0) when the largest of them has not halved over `stall` iterations.
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  long long kernels = 0;
+  ~Graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+// One LOBPCG phase with blocks stored as T for nprob problems (problem p's block at
+// X + p*N*b). Stops per problem when its first nev residuals are <= tol (verified with a
+// fresh H X), when `stall` > 0 and its worst residual has not halved in `stall` iterations,
+// or after maxit lockstep iterations.
 template <typename T>
-iwf_status run_phase(iwf_plan* p, int b, int nev, int maxit, double tol, int stall, void* Xio,
-                     const SmallBufs& sb, Arena& ar, cudaStream_t st, PhaseResult& res) {
+iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxit, double tol,
+                     int stall, void* Xio, Small& sm, Arena& ar, cudaStream_t st,
+                     PhaseResult& res) {
   using V2 = typename Cplx<T>::type;
+  const int np = sm.nprob;
   const long long N = p->g.N;
   const size_t blk = (size_t)N * b;
+  const size_t all = blk * np;
   V2 *X, *HX, *W, *HW, *P, *HP, *X2, *HX2, *P2, *HP2, *W2;
-  T* M;
-  IWF_TRY(ar.get(&HX, blk)); IWF_TRY(ar.get(&W, blk)); IWF_TRY(ar.get(&HW, blk));
-  IWF_TRY(ar.get(&P, blk)); IWF_TRY(ar.get(&HP, blk)); IWF_TRY(ar.get(&X2, blk));
-  IWF_TRY(ar.get(&HX2, blk)); IWF_TRY(ar.get(&P2, blk)); IWF_TRY(ar.get(&HP2, blk));
-  IWF_TRY(ar.get(&W2, blk)); IWF_TRY(ar.get(&M, (size_t)N));
+  IWF_TRY(ar.get(&HX, all)); IWF_TRY(ar.get(&W, all)); IWF_TRY(ar.get(&HW, all));
+  IWF_TRY(ar.get(&P, all)); IWF_TRY(ar.get(&HP, all)); IWF_TRY(ar.get(&X2, all));
+  IWF_TRY(ar.get(&HX2, all)); IWF_TRY(ar.get(&P2, all)); IWF_TRY(ar.get(&HP2, all));
+  IWF_TRY(ar.get(&W2, all));
   X = reinterpret_cast<V2*>(Xio);
-  V2* Xorig = X;
-  const double sigma = p->voff_abs - p->vg0 + 1.0;
-  IWF_TRY(precond_diag<T>(p->d_lam64, p->vg0 + sigma, p->voff_sq, N, M, st));
+  Batch bt{np, (long long)blk, sm.active};
   const int prec = prec_of<T>();
-  std::vector<double> h_resid(b), h_theta(b);
-  int h_status = 0;
+  std::vector<double> h_resid((size_t)np * kMaxBlock), h_theta((size_t)np * kMaxBlock);
+  std::vector<int> h_status(np), h_active(np, 1);
+  res.iters.assign(np, 0);
+  res.converged.assign(np, 0);
+  std::vector<int> pending(np, 0);      // met tol once; waiting for a verified residual
+  std::vector<double> best(np, INFINITY);
+  std::vector<int> best_it(np, 0);
 
-  auto orthonormalize = [&](V2*& Y, V2*& Y2, int* mask) -> iwf_status {
+  auto upload_active = [&]() -> iwf_status {
+    IWF_CUDA(cudaMemcpyAsync(sm.active, h_active.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+    return IWF_OK;
+  };
+  auto count_applies = [&]() {
+    int nact = 0;
+    for (int q = 0; q < np; ++q) nact += h_active[q];
+    res.applies += (long long)b * nact;
+  };
+  auto orthonormalize = [&](V2* Y, V2* Y2, int* mask) -> iwf_status {
     for (int pass = 0; pass < 2; ++pass) {
-      IWF_TRY(gram<T>(blocks({Y}, b), blocks({Y}, b), N, sb.G, sb.partial, sb.slots, st));
-      IWF_TRY(svqb_small(sb.G, b, 1e-14, sb.T, mask, sb.status, st));
-      IWF_TRY(block_update<T>(blocks({Y}, b), N, sb.T, nullptr, b, Y2, nullptr, false, st));
-      std::swap(Y, Y2);
+      IWF_TRY(gram<T>(bt, blocks({Y}, b), blocks({Y}, b), N, sm.G, sm.partial, sm.slots, st));
+      IWF_TRY(svqb_small(bt, sm.G, b, 1e-14, sm.T, mask, sm.status, st));
+      IWF_TRY(block_update<T>(bt, blocks({Y}, b), N, sm.T, nullptr, kCapT, b, Y2, nullptr, false, st));
+      IWF_CUDA(cudaMemcpyAsync(Y, Y2, sizeof(V2) * all, cudaMemcpyDeviceToDevice, st));
     }
     return IWF_OK;
   };
-  // Rayleigh-Ritz on X alone: X <- X Y, HX <- HX Y, theta
-  auto rr_x = [&]() -> iwf_status {
-    IWF_TRY(gram<T>(blocks({X}, b), blocks({HX}, b), N, sb.G, sb.partial, sb.slots, st));
-    IWF_TRY(set_mask(sb.mask, b, 1, st));
-    IWF_TRY(rayleigh_ritz_small(sb.G, b, b, sb.mask, b, sb.theta, sb.Cx, sb.Cp, sb.maskp,
-                                sb.status, st));
-    IWF_TRY(block_update<T>(blocks({X}, b), N, sb.Cx, nullptr, b, X2, nullptr, false, st));
-    IWF_TRY(block_update<T>(blocks({HX}, b), N, sb.Cx, nullptr, b, HX2, nullptr, false, st));
-    std::swap(X, X2);
-    std::swap(HX, HX2);
+  // Rayleigh-Ritz on X alone: X <- X Y, HX <- HX Y, theta (results land back in X, HX)
+  auto rr_x = [&](V2* Xc, V2* HXc, V2* T1, V2* T2) -> iwf_status {
+    IWF_TRY(gram<T>(bt, blocks({Xc}, b), blocks({HXc}, b), N, sm.G, sm.partial, sm.slots, st));
+    IWF_TRY(set_mask(bt, sm.mask, 0, b, 1, nullptr, st));
+    IWF_TRY(rayleigh_ritz_small(bt, sm.G, b, b, sm.mask, b, sm.theta, sm.Cx, sm.Cp, sm.maskp,
+                                sm.status, st));
+    IWF_TRY(block_update<T>(bt, blocks({Xc}, b), N, sm.Cx, nullptr, kCapC, b, T1, nullptr, false, st));
+    IWF_TRY(block_update<T>(bt, blocks({HXc}, b), N, sm.Cx, nullptr, kCapC, b, T2, nullptr, false, st));
+    IWF_CUDA(cudaMemcpyAsync(Xc, T1, sizeof(V2) * all, cudaMemcpyDeviceToDevice, st));
+    IWF_CUDA(cudaMemcpyAsync(HXc, T2, sizeof(V2) * all, cudaMemcpyDeviceToDevice, st));
     return IWF_OK;
   };
-  auto apply = [&](const V2* in, V2* out) -> iwf_status {
-    IWF_TRY(apply_impl(p, prec, in, out, b, st));
-    res.applies += b;
-    return IWF_OK;
+  auto residual = [&](const V2* Xc, const V2* HXc) -> iwf_status {
+    return residual_precond<T>(bt, Xc, HXc, sm.theta, p->d_lam64, sm.shift, sm.off2, W, N, b,
+                               sm.rpartial, sm.slots, sm.resid, st);
+  };
+  // one iteration from (Xa, HXa, Pa, HPa) into (Xb, HXb, Pb, HPb), then the new residual
+  auto iterate = [&](V2* Xa, V2* HXa, V2* Pa, V2* HPa, V2* Xb, V2* HXb, V2* Pb, V2* HPb,
+                     bool hasP) -> iwf_status {
+    for (int pass = 0; pass < 2; ++pass) {
+      const BlockList XP = hasP ? blocks({Xa, Pa}, b) : blocks({Xa}, b);
+      IWF_TRY(gram<T>(bt, XP, blocks({W}, b), N, sm.G, sm.partial, sm.slots, st));
+      IWF_TRY(block_update<T>(bt, XP, N, sm.G, nullptr, kCapG, b, W, nullptr, true, st));
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      IWF_TRY(gram<T>(bt, blocks({W}, b), blocks({W}, b), N, sm.G, sm.partial, sm.slots, st));
+      IWF_TRY(svqb_small(bt, sm.G, b, 1e-14, sm.T, sm.maskw, sm.status, st));
+      IWF_TRY(block_update<T>(bt, blocks({W}, b), N, sm.T, nullptr, kCapT, b, W2, nullptr, false, st));
+      std::swap(W, W2);
+    }
+    IWF_TRY(apply_impl(p, prec, W, HW, b * np, st, nullptr, ab));
+    const int m = hasP ? 3 * b : 2 * b;
+    const BlockList S = hasP ? blocks({Xa, W, Pa}, b) : blocks({Xa, W}, b);
+    const BlockList HS = hasP ? blocks({HXa, HW, HPa}, b) : blocks({HXa, HW}, b);
+    IWF_TRY(gram<T>(bt, S, HS, N, sm.G, sm.partial, sm.slots, st));
+    IWF_TRY(set_mask(bt, sm.mask, 0, b, 1, nullptr, st));
+    IWF_TRY(set_mask(bt, sm.mask, b, b, 0, sm.maskw, st));
+    if (hasP) IWF_TRY(set_mask(bt, sm.mask, 2 * b, b, 0, sm.maskp, st));
+    IWF_TRY(rayleigh_ritz_small(bt, sm.G, m, b, sm.mask, b, sm.theta, sm.Cx, sm.Cp, sm.maskp,
+                                sm.status, st));
+    IWF_TRY(block_update<T>(bt, S, N, sm.Cx, sm.Cp, kCapC, b, Xb, Pb, false, st));
+    IWF_TRY(block_update<T>(bt, HS, N, sm.Cx, sm.Cp, kCapC, b, HXb, HPb, false, st));
+    return residual(Xb, HXb);
   };
   auto read_small = [&]() -> iwf_status {
-    IWF_CUDA(cudaMemcpyAsync(h_resid.data(), sb.resid, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
-    IWF_CUDA(cudaMemcpyAsync(h_theta.data(), sb.theta, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
-    IWF_CUDA(cudaMemcpyAsync(&h_status, sb.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IWF_CUDA(cudaMemcpyAsync(h_resid.data(), sm.resid, sizeof(double) * np * kMaxBlock, cudaMemcpyDeviceToHost, st));
+    IWF_CUDA(cudaMemcpyAsync(h_theta.data(), sm.theta, sizeof(double) * np * kMaxBlock, cudaMemcpyDeviceToHost, st));
+    IWF_CUDA(cudaMemcpyAsync(h_status.data(), sm.status, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
     IWF_CUDA(cudaStreamSynchronize(st));
     return IWF_OK;
   };
-
-  // start: orthonormalise X, apply, Rayleigh-Ritz on X
-  IWF_TRY(orthonormalize(X, X2, sb.maskw));
-  IWF_TRY(apply(X, HX));
-  IWF_TRY(rr_x());
-  bool hasP = false;
-  double best = INFINITY;
-  int best_it = 0;
-  bool verified = false;
-  for (int it = 0; it <= maxit; ++it) {
-    IWF_TRY(residual_precond<T>(X, HX, sb.theta, M, W, N, b, sb.rpartial, sb.slots, sb.resid, st));
-    IWF_TRY(read_small());
-    if (h_status != 0) return fail(IWF_ERR_BREAKDOWN, "Rayleigh-Ritz subspace lost rank");
-    double worst = 0;
+  auto worst_of = [&](int q) {
+    double w = 0;
     for (int j = 0; j < nev; ++j) {
-      if (!std::isfinite(h_resid[j]) || !std::isfinite(h_theta[j]))
-        return fail(IWF_ERR_NONFINITE, "non-finite residual in the eigensolver");
-      worst = std::max(worst, h_resid[j]);
+      const double r = h_resid[(size_t)q * kMaxBlock + j];
+      w = std::isfinite(r) ? std::max(w, r) : INFINITY;
     }
-    res.iters = it;
-    if (log_level() > 0) {
-      std::fprintf(stderr, "[iwf] %s it %d worst %.3e theta0 %.12f theta%d %.12f\n",
-                   sizeof(T) == 8 ? "f64" : "c64", it, worst, h_theta[0], nev - 1, h_theta[nev - 1]);
-      if (log_level() > 1) {
-        for (int j = 0; j < b; ++j) std::fprintf(stderr, " %.2e", h_resid[j]);
-        std::fprintf(stderr, "\n");
+    return w;
+  };
+
+  IWF_TRY(upload_active());
+  IWF_CUDA(cudaMemsetAsync(sm.status, 0, sizeof(int) * np, st));
+  IWF_TRY(orthonormalize(X, X2, sm.maskw));
+  count_applies();
+  IWF_TRY(apply_impl(p, prec, X, HX, b * np, st, nullptr, ab));
+  IWF_TRY(rr_x(X, HX, X2, HX2));
+  IWF_TRY(residual(X, HX));
+  bool hasP = false;
+  int parity = 0;                // 0: current iterate in (X, HX, P, HP), 1: in the *2 set
+  Graph graphs[2];
+  for (int it = 0;; ++it) {
+    IWF_TRY(read_small());
+    bool any_pending = false, any_active = false;
+    for (int q = 0; q < np; ++q) {
+      if (!h_active[q]) continue;
+      if (h_status[q] != 0) return fail(IWF_ERR_BREAKDOWN, "Rayleigh-Ritz subspace lost rank");
+      const double w = worst_of(q);
+      if (!std::isfinite(w)) return fail(IWF_ERR_NONFINITE, "non-finite residual in the eigensolver");
+      res.iters[q] = it;
+      if (w <= tol) {
+        if (pending[q]) { res.converged[q] = 1; h_active[q] = 0; pending[q] = 0; continue; }
+        pending[q] = 1;
+        any_pending = true;
+      } else {
+        pending[q] = 0;
+        if (stall > 0) {
+          if (w < 0.5 * best[q]) { best[q] = w; best_it[q] = it; }
+          else if (it - best_it[q] >= stall) { h_active[q] = 0; continue; }
+        }
       }
+      any_active = true;
     }
-    if (worst <= tol) {
-      if (verified) { res.converged = true; break; }
-      // recompute H X explicitly (removes drift of the implicit HX updates), re-check
-      IWF_TRY(apply(X, HX));
-      IWF_TRY(rr_x());
-      verified = true;
+    if (log_level() > 0) {
+      int nact = 0;
+      double worst = 0;
+      for (int q = 0; q < np; ++q) if (h_active[q]) { ++nact; worst = std::max(worst, worst_of(q)); }
+      std::fprintf(stderr, "[iwf] %s it %d active %d worst %.3e theta0 %.12f\n",
+                   sizeof(T) == 8 ? "f64" : "c64", it, nact, worst, h_theta[0]);
+      if (log_level() > 1)
+        for (int q = 0; q < np; ++q) {
+          for (int j = 0; j < b; ++j) std::fprintf(stderr, " %.2e", h_resid[(size_t)q * kMaxBlock + j]);
+          std::fprintf(stderr, "\n");
+        }
+    }
+    res.rounds = it;
+    if (!any_active || it >= maxit) break;
+    IWF_TRY(upload_active());
+    V2 *Xa = parity ? X2 : X, *HXa = parity ? HX2 : HX, *Pa = parity ? P2 : P, *HPa = parity ? HP2 : HP;
+    V2 *Xb = parity ? X : X2, *HXb = parity ? HX : HX2, *Pb = parity ? P : P2, *HPb = parity ? HP : HP2;
+    if (any_pending) {
+      // fresh H X for every active problem (removes drift of the implicit HX updates); the
+      // spare buffer set (Xb, HXb) is scratch here
+      count_applies();
+      IWF_TRY(apply_impl(p, prec, Xa, HXa, b * np, st, nullptr, ab));
+      IWF_TRY(rr_x(Xa, HXa, Xb, HXb));
+      IWF_TRY(residual(Xa, HXa));
       --it;
       continue;
     }
-    verified = false;
-    if (it == maxit) break;
-    if (stall > 0) {
-      if (worst < 0.5 * best) { best = worst; best_it = it; }
-      else if (it - best_it >= stall) break;
+    count_applies();
+    if (hasP && graphs_enabled()) {
+      Graph& g = graphs[parity];
+      if (!g.exec) {
+        const long long k0 = launch_count();
+        IWF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const iwf_status s = iterate(Xa, HXa, Pa, HPa, Xb, HXb, Pb, HPb, true);
+        const cudaError_t e = cudaStreamEndCapture(st, &g.graph);
+        if (s != IWF_OK) return s;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        IWF_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+        g.kernels = launch_count() - k0;
+      } else {
+        for (long long k = 0; k < g.kernels; ++k) count_launch();
+      }
+      IWF_CUDA(cudaGraphLaunch(g.exec, st));
+    } else {
+      IWF_TRY(iterate(Xa, HXa, Pa, HPa, Xb, HXb, Pb, HPb, hasP));
     }
-    // W <- W - [X P]([X P]^H W), twice
-    for (int pass = 0; pass < 2; ++pass) {
-      const BlockList XP = hasP ? blocks({X, P}, b) : blocks({X}, b);
-      IWF_TRY(gram<T>(XP, blocks({W}, b), N, sb.G, sb.partial, sb.slots, st));
-      IWF_TRY(block_update<T>(XP, N, sb.G, nullptr, b, W, nullptr, true, st));
-    }
-    IWF_TRY(orthonormalize(W, W2, sb.maskw));
-    IWF_TRY(apply(W, HW));
-    const int m = hasP ? 3 * b : 2 * b;
-    const BlockList S = hasP ? blocks({X, W, P}, b) : blocks({X, W}, b);
-    const BlockList HS = hasP ? blocks({HX, HW, HP}, b) : blocks({HX, HW}, b);
-    IWF_TRY(gram<T>(S, HS, N, sb.G, sb.partial, sb.slots, st));
-    IWF_TRY(set_mask(sb.mask, b, 1, st));
-    IWF_CUDA(cudaMemcpyAsync(sb.mask + b, sb.maskw, sizeof(int) * b, cudaMemcpyDeviceToDevice, st));
-    if (hasP)
-      IWF_CUDA(cudaMemcpyAsync(sb.mask + 2 * b, sb.maskp, sizeof(int) * b, cudaMemcpyDeviceToDevice, st));
-    IWF_TRY(rayleigh_ritz_small(sb.G, m, b, sb.mask, b, sb.theta, sb.Cx, sb.Cp, sb.maskp,
-                                sb.status, st));
-    IWF_TRY(block_update<T>(S, N, sb.Cx, sb.Cp, b, X2, P2, false, st));
-    IWF_TRY(block_update<T>(HS, N, sb.Cx, sb.Cp, b, HX2, HP2, false, st));
-    std::swap(X, X2); std::swap(HX, HX2); std::swap(P, P2); std::swap(HP, HP2);
     hasP = true;
+    parity ^= 1;
   }
   res.theta = h_theta;
   res.resid = h_resid;
-  if (X != Xorig)
-    IWF_CUDA(cudaMemcpyAsync(Xorig, X, sizeof(V2) * blk, cudaMemcpyDeviceToDevice, st));
+  if (parity)
+    IWF_CUDA(cudaMemcpyAsync(X, X2, sizeof(V2) * all, cudaMemcpyDeviceToDevice, st));
   IWF_CUDA(cudaStreamSynchronize(st));
   return IWF_OK;
 }
 
-}  // namespace
+// Shared driver: problems 0..np-1 with preconditioner parameters already on the device.
+iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opts* o,
+                          Small& sm, Arena& ar, const void* X0, double* evals, void* evecs,
+                          double* resid, int* iters_out, iwf_solve_info* info, cudaStream_t st) {
+  const int np = sm.nprob;
+  const int nev = o->nev;
+  const int b = o->block > 0 ? o->block : nev;
+  const double tol = o->tol > 0 ? o->tol : 1e-10;
+  const int maxit = o->maxit > 0 ? o->maxit : 1000;
+  const long long N = p->g.N;
+  const size_t all = (size_t)N * b * np;
+  const auto t0 = std::chrono::steady_clock::now();
+  double2* X;
+  IWF_TRY(ar.get(&X, all));
+  PhaseResult r1, r2;
+  if (o->precision == IWF_PREC_C64) {
+    float2* Xf;
+    IWF_TRY(ar.get(&Xf, all));
+    if (X0) IWF_TRY((convert_block<double, float>(X0, Xf, 2 * (long long)all, st)));
+    else IWF_TRY(random_block<float>(Xf, N, b * np, o->seed, st));
+    const double tol1 = std::max(tol, o->c64_tol > 0 ? o->c64_tol : 1e-4);
+    IWF_TRY(run_phase<float>(p, ab, b, nev, maxit, tol1, 5, Xf, sm, ar, st, r1));
+    IWF_TRY((convert_block<float, double>(Xf, X, 2 * (long long)all, st)));
+  } else {
+    if (X0) IWF_CUDA(cudaMemcpyAsync(X, X0, sizeof(double2) * all, cudaMemcpyDeviceToDevice, st));
+    else IWF_TRY(random_block<double>(X, N, b * np, o->seed, st));
+  }
+  const int left = std::max(1, maxit - r1.rounds);
+  IWF_TRY(run_phase<double>(p, ab, b, nev, left, tol, 0, X, sm, ar, st, r2));
+  if (evecs) {
+    for (int q = 0; q < np; ++q)
+      IWF_CUDA(cudaMemcpyAsync(reinterpret_cast<double2*>(evecs) + (size_t)q * N * nev,
+                               X + (size_t)q * N * b, sizeof(double2) * N * nev,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  IWF_CUDA(cudaStreamSynchronize(st));
+  bool all_conv = true;
+  double worst = 0;
+  for (int q = 0; q < np; ++q) {
+    for (int j = 0; j < nev; ++j) {
+      evals[(size_t)q * nev + j] = r2.theta[(size_t)q * kMaxBlock + j];
+      const double r = r2.resid[(size_t)q * kMaxBlock + j];
+      if (resid) resid[(size_t)q * nev + j] = r;
+      worst = std::max(worst, r);
+    }
+    if (iters_out) iters_out[q] = (r1.iters.empty() ? 0 : r1.iters[q]) + r2.iters[q];
+    all_conv = all_conv && r2.converged[q];
+  }
+  if (info) {
+    info->iters = r1.rounds + r2.rounds;
+    info->iters_c64 = r1.rounds;
+    info->applies = r1.applies + r2.applies;
+    info->converged = all_conv ? 1 : 0;
+    info->max_resid = worst;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!all_conv) return fail(IWF_ERR_NOCONV, "eigensolver reached maxit before tol");
+  return IWF_OK;
+}
 
-iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
-                           void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st) {
+iwf_status check_opts(const iwf_plan* p, const iwf_solve_opts* o) {
   if (!o) return fail(IWF_ERR_ARG, "iwf_eigensolve: NULL options");
   const int nev = o->nev;
   const int b = o->block > 0 ? o->block : nev;
   if (nev < 1 || b < nev || b > kMaxBlock)
     return fail(IWF_ERR_ARG, "iwf_eigensolve: need 1 <= nev <= block <= 24");
   if ((long long)3 * b > p->g.N) return fail(IWF_ERR_ARG, "iwf_eigensolve: window too small for the block");
-  if (!evals || !evecs) return fail(IWF_ERR_ARG, "iwf_eigensolve: NULL output");
-  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_eigensolve: no potential set");
   if (o->precision != IWF_PREC_F64 && o->precision != IWF_PREC_C64)
     return fail(IWF_ERR_ARG, "iwf_eigensolve: unknown precision");
-  const double tol = o->tol > 0 ? o->tol : 1e-10;
-  const int maxit = o->maxit > 0 ? o->maxit : 1000;
-  const long long N = p->g.N;
-  const auto t0 = std::chrono::steady_clock::now();
-
-  Arena ar;
-  SmallBufs sb;
-  IWF_TRY(alloc_small(ar, sb));
-  double2* X;
-  IWF_TRY(ar.get(&X, (size_t)N * b));
-  PhaseResult r1, r2;
-  if (o->precision == IWF_PREC_C64) {
-    float2* Xf;
-    IWF_TRY(ar.get(&Xf, (size_t)N * b));
-    if (X0) IWF_TRY((convert_block<double, float>(X0, Xf, 2 * N * b, st)));
-    else IWF_TRY(random_block<float>(Xf, N, b, o->seed, st));
-    const double tol1 = std::max(tol, o->c64_tol > 0 ? o->c64_tol : 1e-4);
-    IWF_TRY(run_phase<float>(p, b, nev, maxit, tol1, 5, Xf, sb, ar, st, r1));
-    IWF_TRY((convert_block<float, double>(Xf, X, 2 * N * b, st)));
-  } else {
-    if (X0) IWF_CUDA(cudaMemcpyAsync(X, X0, sizeof(double2) * N * b, cudaMemcpyDeviceToDevice, st));
-    else IWF_TRY(random_block<double>(X, N, b, o->seed, st));
-  }
-  IWF_TRY(run_phase<double>(p, b, nev, std::max(1, maxit - r1.iters), tol, 0, X, sb, ar, st, r2));
-  IWF_CUDA(cudaMemcpyAsync(evecs, X, sizeof(double2) * N * nev, cudaMemcpyDeviceToDevice, st));
-  IWF_CUDA(cudaStreamSynchronize(st));
-  for (int j = 0; j < nev; ++j) {
-    evals[j] = r2.theta[j];
-    if (resid) resid[j] = r2.resid[j];
-  }
-  if (info) {
-    info->iters = r1.iters + r2.iters;
-    info->iters_c64 = r1.iters;
-    info->applies = r1.applies + r2.applies;
-    info->converged = r2.converged ? 1 : 0;
-    double w = 0;
-    for (int j = 0; j < nev; ++j) w = std::max(w, r2.resid[j]);
-    info->max_resid = w;
-    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  if (!r2.converged) return fail(IWF_ERR_NOCONV, "eigensolver reached maxit before tol");
   return IWF_OK;
+}
+
+// The solve runs on a library stream ordered after the caller's stream (so it can be
+// captured into graphs whatever stream the caller uses).
+struct SolveStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  ~SolveStream() {
+    if (ev) cudaEventDestroy(ev);
+    if (s) cudaStreamDestroy(s);
+  }
+  iwf_status open(cudaStream_t caller) {
+    IWF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    IWF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    IWF_CUDA(cudaEventRecord(ev, caller));
+    IWF_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    return IWF_OK;
+  }
+};
+
+}  // namespace
+
+iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
+                           void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st) {
+  IWF_TRY(check_opts(p, o));
+  if (!evals || !evecs) return fail(IWF_ERR_ARG, "iwf_eigensolve: NULL output");
+  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_eigensolve: no potential set");
+  SolveStream ss;
+  IWF_TRY(ss.open(st));
+  Arena ar;
+  Small sm;
+  IWF_TRY(alloc_small(ar, sm, 1));
+  const double sigma = p->voff_abs - p->vg0 + 1.0;
+  const double shift = p->vg0 + sigma, off2 = p->voff_sq;
+  IWF_CUDA(cudaMemcpyAsync(sm.shift, &shift, sizeof(double), cudaMemcpyHostToDevice, ss.s));
+  IWF_CUDA(cudaMemcpyAsync(sm.off2, &off2, sizeof(double), cudaMemcpyHostToDevice, ss.s));
+  int iters = 0;
+  return solve_problems(p, nullptr, o, sm, ar, X0, evals, evecs, resid, &iters, info, ss.s);
+}
+
+iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, const int* m,
+                                 const double* re, const double* im, const iwf_solve_opts* o,
+                                 double* evals, void* evecs, double* resid, int* iters,
+                                 iwf_solve_info* info, cudaStream_t st) {
+  IWF_TRY(check_opts(p, o));
+  if (nprob < 1 || !nmodes || !evals) return fail(IWF_ERR_ARG, "iwf_batch_eigensolve: bad arguments");
+  const int b = o->block > 0 ? o->block : o->nev;
+  if ((long long)nprob * b > 65535) return fail(IWF_ERR_ARG, "iwf_batch_eigensolve: nprob * block > 65535");
+  SolveStream ss;
+  IWF_TRY(ss.open(st));
+  Arena ar;
+  Small sm;
+  IWF_TRY(alloc_small(ar, sm, nprob));
+  long long stride = 0;
+  for (int j = 0; j < p->g.n; ++j) stride += p->g.lens[j];
+  double* tab64;
+  float* tab32;
+  IWF_TRY(ar.get(&tab64, (size_t)nprob * stride));
+  IWF_TRY(ar.get(&tab32, (size_t)nprob * stride));
+  std::vector<double> shift(nprob), off2(nprob);
+  long long mo = 0;
+  for (int q = 0; q < nprob; ++q) {
+    if (nmodes[q] < 0 || (nmodes[q] > 0 && (!m || !re || !im)))
+      return fail(IWF_ERR_ARG, "iwf_batch_eigensolve: bad mode list");
+    PotSummary s;
+    IWF_TRY(potential_tables(p, nmodes[q], m + mo * p->g.n, re + mo, im + mo,
+                             tab64 + (size_t)q * stride, tab32 + (size_t)q * stride, &s, ss.s));
+    const double sigma = s.off_abs - s.vg0 + 1.0;
+    shift[q] = s.vg0 + sigma;
+    off2[q] = s.off_sq;
+    mo += nmodes[q];
+  }
+  IWF_CUDA(cudaMemcpyAsync(sm.shift, shift.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice, ss.s));
+  IWF_CUDA(cudaMemcpyAsync(sm.off2, off2.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice, ss.s));
+  ApplyBatch ab{tab64, tab32, stride, b, sm.active};
+  return solve_problems(p, &ab, o, sm, ar, nullptr, evals, evecs, resid, iters, info, ss.s);
 }
 
 }  // namespace iwf

@@ -6,6 +6,7 @@
 // and sum rounded separately (__dmul_rn / __dadd_rn, no contraction), so the
 // classification is reproducible. The true index of window position t in a slice is
 // k_j = lo_j + t_j, which is the inverse of the index-shift map rho (Eqs. inverse1-3).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -132,7 +133,7 @@ __device__ double mode_sum(const ModeArgs& a, const int* l) {
 
 // Per-axis tables: entry (axis j, l) = V restricted to the modes on axis j, at y_j = 2 pi l/len_j.
 __global__ void axis_table_kernel(ModeArgs a, const int* mode_axis, int total, const int* tab_axis,
-                                  const int* tab_l, double* t64, float* t32) {
+                                  const int* tab_l, double* t64, float* t32, int fold_const) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int ax = tab_axis[i];
@@ -140,6 +141,7 @@ __global__ void axis_table_kernel(ModeArgs a, const int* mode_axis, int total, c
   l[ax] = tab_l[i];
   double v = 0.0;
   for (int q = 0; q < a.nmodes; ++q) {
+    if (fold_const && ax == 0 && mode_axis[q] < 0) { v += a.re[q]; continue; }
     if (mode_axis[q] != ax) continue;
     const int len = a.g.lens[ax];
     const int ph = (int)(((long long)a.m[q * a.g.n + ax] * l[ax]) % len);
@@ -215,13 +217,23 @@ iwf_status export_window(const iwf_plan* p, int* k_host) {
   return IWF_OK;
 }
 
-iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
-                           const double* im) {
-  const Geom& g = p->g;
+namespace {
+struct Folded {
+  std::vector<int> m;          // modes reduced to [0, len_j), merged
+  std::vector<double> re, im;
+  std::vector<int> axis;       // -1 constant, j single-axis, -2 several axes
+  double vg0 = 0, off_abs = 0, off_sq = 0, vconst = 0;
+  bool separable = true;
+};
+
+// Fold the modes onto the grid (aliasing rule), merge duplicates, check that V is real and
+// classify every mode by the lifted axes it touches.
+iwf_status fold_modes(const Geom& g, int nmodes, const int* m, const double* re,
+                      const double* im, Folded& out) {
   const int n = g.n;
-  // fold every mode onto the grid (aliasing rule) and merge duplicates
-  std::vector<int> fm;
-  std::vector<double> fre, fim;
+  std::vector<int>& fm = out.m;
+  std::vector<double>& fre = out.re;
+  std::vector<double>& fim = out.im;
   for (int q = 0; q < nmodes; ++q) {
     if (!std::isfinite(re[q]) || !std::isfinite(im[q]))
       return fail(IWF_ERR_NONFINITE, "iwf_set_potential: non-finite coefficient");
@@ -263,22 +275,33 @@ iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* 
                                "pairs with conjugate coefficients)");
   }
   // preconditioner summaries and the axis classification
-  double vg0 = 0.0, off_abs = 0.0, off_sq = 0.0, vconst = 0.0;
-  std::vector<int> mode_axis(fre.size(), -1);
-  bool separable = true;
-  std::vector<int> um;
-  std::vector<double> ure, uim;
+  out.axis.assign(fre.size(), -1);
   for (size_t r = 0; r < fre.size(); ++r) {
     int nz = 0, ax = -1;
     for (int j = 0; j < n; ++j) if (fm[r * n + j] != 0) { ++nz; ax = j; }
     const double a2 = fre[r] * fre[r] + fim[r] * fim[r];
-    if (nz == 0) { vg0 = fre[r]; vconst = fre[r]; continue; }
-    off_abs += std::sqrt(a2);
-    off_sq += a2;
-    if (nz > 1) separable = false;
-    mode_axis[r] = ax;
+    if (nz == 0) { out.vg0 = fre[r]; out.vconst = fre[r]; continue; }
+    out.off_abs += std::sqrt(a2);
+    out.off_sq += a2;
+    if (nz > 1) { out.separable = false; ax = -2; }
+    out.axis[r] = ax;
   }
-  p->vg0 = vg0; p->voff_abs = off_abs; p->voff_sq = off_sq; p->vconst = vconst;
+  return IWF_OK;
+}
+}  // namespace
+
+iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
+                           const double* im) {
+  const Geom& g = p->g;
+  const int n = g.n;
+  Folded F;
+  IWF_TRY(fold_modes(g, nmodes, m, re, im, F));
+  const std::vector<int>& fm = F.m;
+  const std::vector<double>& fre = F.re;
+  const std::vector<double>& fim = F.im;
+  const std::vector<int>& mode_axis = F.axis;
+  const bool separable = F.separable;
+  p->vg0 = F.vg0; p->voff_abs = F.off_abs; p->voff_sq = F.off_sq; p->vconst = F.vconst;
 
   DevBuf<int> d_m, d_axis, d_tax, d_tl;
   DevBuf<double> d_re, d_im;
@@ -316,7 +339,7 @@ iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* 
     IWF_CUDA(cudaMemcpy(d_tax.p, tax.data(), total * sizeof(int), cudaMemcpyHostToDevice));
     IWF_CUDA(cudaMemcpy(d_tl.p, tl.data(), total * sizeof(int), cudaMemcpyHostToDevice));
     axis_table_kernel<<<(total + T - 1) / T, T>>>(a, d_axis.p, total, d_tax.p, d_tl.p,
-                                                  p->d_tab64, p->d_tab32);
+                                                  p->d_tab64, p->d_tab32, 0);
     IWF_CUDA(cudaGetLastError());
     p->pot_kind = 1;
   } else {
@@ -327,6 +350,50 @@ iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* 
     p->pot_kind = 2;
   }
   IWF_CUDA(cudaDeviceSynchronize());
+  return IWF_OK;
+}
+
+iwf_status potential_tables(const iwf_plan* p, int nmodes, const int* m, const double* re,
+                            const double* im, double* tab64, float* tab32, PotSummary* sum,
+                            cudaStream_t s) {
+  const Geom& g = p->g;
+  const int n = g.n;
+  Folded F;
+  IWF_TRY(fold_modes(g, nmodes, m, re, im, F));
+  if (!F.separable)
+    return fail(IWF_ERR_UNSUPPORTED, "batched solves need potentials whose modes each lie on one "
+                                     "lifted axis");
+  sum->vg0 = F.vg0; sum->off_abs = F.off_abs; sum->off_sq = F.off_sq; sum->separable = true;
+  const size_t nm = F.re.size();
+  std::vector<int> tax, tl;
+  int total = 0;
+  for (int j = 0; j < n; ++j) {
+    for (int l = 0; l < g.lens[j]; ++l) { tax.push_back(j); tl.push_back(l); }
+    total += g.lens[j];
+  }
+  DevBuf<int> d_m, d_axis, d_tax, d_tl;
+  DevBuf<double> d_re, d_im;
+  IWF_CUDA(cudaMalloc((void**)&d_m.p, std::max<size_t>(nm, 1) * n * sizeof(int)));
+  IWF_CUDA(cudaMalloc((void**)&d_axis.p, std::max<size_t>(nm, 1) * sizeof(int)));
+  IWF_CUDA(cudaMalloc((void**)&d_re.p, std::max<size_t>(nm, 1) * sizeof(double)));
+  IWF_CUDA(cudaMalloc((void**)&d_im.p, std::max<size_t>(nm, 1) * sizeof(double)));
+  IWF_CUDA(cudaMalloc((void**)&d_tax.p, total * sizeof(int)));
+  IWF_CUDA(cudaMalloc((void**)&d_tl.p, total * sizeof(int)));
+  if (nm) {
+    IWF_CUDA(cudaMemcpy(d_m.p, F.m.data(), nm * n * sizeof(int), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_axis.p, F.axis.data(), nm * sizeof(int), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_re.p, F.re.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(d_im.p, F.im.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  IWF_CUDA(cudaMemcpy(d_tax.p, tax.data(), total * sizeof(int), cudaMemcpyHostToDevice));
+  IWF_CUDA(cudaMemcpy(d_tl.p, tl.data(), total * sizeof(int), cudaMemcpyHostToDevice));
+  ModeArgs a{};
+  a.g = g; a.nmodes = (int)nm; a.m = d_m.p; a.re = d_re.p; a.im = d_im.p;
+  a.scale = 1.0 / (double)g.N;
+  axis_table_kernel<<<(total + 255) / 256, 256, 0, s>>>(a, d_axis.p, total, d_tax.p, d_tl.p,
+                                                        tab64, tab32, 1);
+  IWF_CUDA(cudaGetLastError());
+  IWF_CUDA(cudaStreamSynchronize(s));
   return IWF_OK;
 }
 
