@@ -186,12 +186,61 @@ iwf_status iwf_eigensolve(iwf_plan* plan, const iwf_solve_opts* opts, const void
  *   evecs   device, nprob*N*nev complex doubles (problem p at offset p*N*nev), or NULL.
  *   iters   host, nprob ints (may be NULL): iterations each problem needed.
  *   info    host (may be NULL): totals over the batch (iters = lockstep iterations).
- * The start block is the seeded random one. nprob * block <= 65535. Synchronises `stream`.
+ *   X0      device, nprob*block*N complex doubles (problem p's start block at p*block*N,
+ *           column-major, window order) or NULL for the seeded random start.
+ * nprob * block <= 65535. Synchronises `stream`.
  */
 iwf_status iwf_batch_eigensolve(iwf_plan* plan, int nprob, const int* nmodes, const int* m,
                                 const double* re, const double* im, const iwf_solve_opts* opts,
-                                double* evals, void* evecs, double* resid, int* iters,
-                                iwf_solve_info* info, void* stream);
+                                const void* X0, double* evals, void* evecs, double* resid,
+                                int* iters, iwf_solve_info* info, void* stream);
+
+/*
+ * Learned warm start (no counterpart in the paper, whose start vector is e_1; Sec. 4.1):
+ * an MLP from a potential's parameters to the lowest eigenvectors on a small "core" window.
+ * Dense layers use bfloat16 weights and inputs with float32 accumulation on the tensor
+ * cores, GELU between layers, a linear output; float32 master weights and AdamW.
+ *   dims: nlayers+1 sizes, every one a multiple of 64 (pad the features with zeros).
+ *   Output layout per sample: 2*nvec*ncore floats, (v*ncore + i)*2 + {0: re, 1: im}.
+ * Loss per sample: |X X^H - Y Y^H|_F^2 / nvec for reference X and prediction Y on the core,
+ * averaged over the batch (independent of each eigenvector's phase and of rotations inside
+ * degenerate eigenspaces). Parameters are one flat float32 vector: per layer W (out x in,
+ * row-major) then b (out). Batch sizes are multiples of 64. All pointers are device
+ * pointers unless named host.
+ */
+typedef struct iwf_ws iwf_ws;
+iwf_status iwf_ws_create(iwf_ws** ws, int nlayers, const int* dims, unsigned long long seed,
+                         int device);
+void iwf_ws_destroy(iwf_ws* ws);
+iwf_status iwf_ws_num_params(const iwf_ws* ws, long long* n);
+iwf_status iwf_ws_get_params(const iwf_ws* ws, float* host);            /* host nparams */
+iwf_status iwf_ws_set_params(iwf_ws* ws, const float* host);            /* host nparams */
+/* out (nsamples x dims[nlayers]) = MLP(feat (nsamples x dims[0])). */
+iwf_status iwf_ws_predict(iwf_ws* ws, int nsamples, const float* feat, float* out, void* stream);
+/* Loss (host scalar, may be NULL) and gradient (host nparams, may be NULL) of one batch. */
+iwf_status iwf_ws_loss_grad(iwf_ws* ws, int nsamples, const float* feat, const float* target,
+                            int nvec, int ncore, float* loss, float* grads_host, void* stream);
+/* AdamW (beta 0.9/0.999, eps 1e-8, weight decay wd on W only) over shuffled batches;
+   loss_hist host (epochs), mean batch loss per epoch (may be NULL). Synchronises. */
+iwf_status iwf_ws_train(iwf_ws* ws, int nsamples, const float* feat, const float* target,
+                        int nvec, int ncore, int epochs, int batch, float lr, float wd,
+                        unsigned long long seed, float* loss_hist, void* stream);
+/*
+ * Embed vectors on the window of plan `core` into the window of plan `big` by true index k
+ * (zero elsewhere). in: nprob*nvec vectors of core N; out: nprob*nvec vectors of big N
+ * (complex double). The core window must lie inside the big one (IWF_ERR_ARG otherwise).
+ */
+iwf_status iwf_ws_embed(const iwf_plan* core, const iwf_plan* big, int nprob, int nvec,
+                        const void* in, void* out, void* stream);
+/*
+ * vecs[p][v][k] *= exp(i * sign * k . phi_p) on the plan's window (true index k), in place:
+ * nprob*nvec complex-double vectors, phases host nprob*n doubles, sign = +1 or -1.
+ * A shift of the potential's phases, V(y) = sum_m c_m e^{i m.(y + phi)}, is this diagonal
+ * unitary (H_phi = D H_0 D^H, D = diag(e^{i k.phi})) up to the grid wrap-around, so the
+ * warm-start network needs to learn only the phase-free problem. Synchronises `stream`.
+ */
+iwf_status iwf_ws_phase(const iwf_plan* plan, int nprob, int nvec, const double* phases,
+                        int sign, void* vecs, void* stream);
 
 /*
  * Same computation as iwf_apply, with CUDA events recorded on `stream` around every pass

@@ -165,7 +165,7 @@ class Plan:
 
     def batch_eigensolve(self, potentials, nev, block=0, tol=1e-10, maxit=0, precision="f64",
                          c64_tol=0.0, seed=1, want_vectors=False, stream=None,
-                         raise_noconv=True):
+                         raise_noconv=True, X0=None):
         """iwf_batch_eigensolve over [(modes, coef), ...] sharing this plan's geometry.
 
         Returns (evals (nprob, nev), evecs (nprob, nev, N) or None, resid, iters, info)."""
@@ -193,6 +193,7 @@ class Plan:
             self.handle, nprob, nm.ctypes.data_as(C.POINTER(C.c_int)),
             modes.ctypes.data_as(C.POINTER(C.c_int)), re.ctypes.data_as(C.POINTER(C.c_double)),
             im.ctypes.data_as(C.POINTER(C.c_double)), C.byref(opts),
+            C.c_void_p(X0.data_ptr()) if X0 is not None else None,
             evals.ctypes.data_as(C.POINTER(C.c_double)),
             C.c_void_p(evecs.data_ptr()) if evecs is not None else None,
             resid.ctypes.data_as(C.POINTER(C.c_double)), iters.ctypes.data_as(C.POINTER(C.c_int)),

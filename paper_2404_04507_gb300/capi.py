@@ -71,9 +71,21 @@ _PROTOS = {
     "iwf_eigensolve": (_i, [_vp, C.POINTER(iwf_solve_opts), _vp, C.POINTER(C.c_double), _vp,
                             C.POINTER(C.c_double), C.POINTER(iwf_solve_info), _vp]),
     "iwf_batch_eigensolve": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(C.c_double),
-                                  C.POINTER(C.c_double), C.POINTER(iwf_solve_opts),
+                                  C.POINTER(C.c_double), C.POINTER(iwf_solve_opts), _vp,
                                   C.POINTER(C.c_double), _vp, C.POINTER(C.c_double),
                                   C.POINTER(_i), C.POINTER(iwf_solve_info), _vp]),
+    "iwf_ws_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_i), C.c_ulonglong, _i]),
+    "iwf_ws_destroy": (None, [_vp]),
+    "iwf_ws_num_params": (_i, [_vp, C.POINTER(_ll)]),
+    "iwf_ws_get_params": (_i, [_vp, C.POINTER(C.c_float)]),
+    "iwf_ws_set_params": (_i, [_vp, C.POINTER(C.c_float)]),
+    "iwf_ws_predict": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "iwf_ws_loss_grad": (_i, [_vp, _i, _vp, _vp, _i, _i, C.POINTER(C.c_float),
+                              C.POINTER(C.c_float), _vp]),
+    "iwf_ws_train": (_i, [_vp, _i, _vp, _vp, _i, _i, _i, _i, C.c_float, C.c_float,
+                          C.c_ulonglong, C.POINTER(C.c_float), _vp]),
+    "iwf_ws_embed": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "iwf_ws_phase": (_i, [_vp, _i, _i, C.POINTER(C.c_double), _i, _vp, _vp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _fn = getattr(lib, _name)

@@ -238,13 +238,13 @@ long long iwf_kernel_launches(void) { return launch_count(); }
 
 iwf_status iwf_batch_eigensolve(iwf_plan* p, int nprob, const int* nmodes, const int* m,
                                 const double* re, const double* im, const iwf_solve_opts* opts,
-                                double* evals, void* evecs, double* resid, int* iters,
-                                iwf_solve_info* info, void* stream) {
+                                const void* X0, double* evals, void* evecs, double* resid,
+                                int* iters, iwf_solve_info* info, void* stream) {
   clear_error();
   if (!p) return fail(IWF_ERR_ARG, "iwf_batch_eigensolve: NULL plan");
   DeviceGuard guard(p->device);
-  return batch_eigensolve_impl(p, nprob, nmodes, m, re, im, opts, evals, evecs, resid, iters,
-                               info, (cudaStream_t)stream);
+  return batch_eigensolve_impl(p, nprob, nmodes, m, re, im, opts, X0, evals, evecs, resid,
+                               iters, info, (cudaStream_t)stream);
 }
 
 iwf_status iwf_eigensolve(iwf_plan* p, const iwf_solve_opts* opts, const void* X0, double* evals,

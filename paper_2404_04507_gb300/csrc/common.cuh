@@ -127,8 +127,8 @@ iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0,
                            void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st);
 iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, const int* m,
                                  const double* re, const double* im, const iwf_solve_opts* o,
-                                 double* evals, void* evecs, double* resid, int* iters,
-                                 iwf_solve_info* info, cudaStream_t st);
+                                 const void* X0, double* evals, void* evecs, double* resid,
+                                 int* iters, iwf_solve_info* info, cudaStream_t st);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties

@@ -426,8 +426,8 @@ iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0,
 
 iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, const int* m,
                                  const double* re, const double* im, const iwf_solve_opts* o,
-                                 double* evals, void* evecs, double* resid, int* iters,
-                                 iwf_solve_info* info, cudaStream_t st) {
+                                 const void* X0, double* evals, void* evecs, double* resid,
+                                 int* iters, iwf_solve_info* info, cudaStream_t st) {
   IWF_TRY(check_opts(p, o));
   if (nprob < 1 || !nmodes || !evals) return fail(IWF_ERR_ARG, "iwf_batch_eigensolve: bad arguments");
   const int b = o->block > 0 ? o->block : o->nev;
@@ -459,7 +459,7 @@ iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, cons
   IWF_CUDA(cudaMemcpyAsync(sm.shift, shift.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice, ss.s));
   IWF_CUDA(cudaMemcpyAsync(sm.off2, off2.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice, ss.s));
   ApplyBatch ab{tab64, tab32, stride, b, sm.active};
-  return solve_problems(p, &ab, o, sm, ar, nullptr, evals, evecs, resid, iters, info, ss.s);
+  return solve_problems(p, &ab, o, sm, ar, X0, evals, evecs, resid, iters, info, ss.s);
 }
 
 }  // namespace iwf

@@ -174,3 +174,23 @@ def random_modes(n: int, count: int, radius: int, seed: int):
         modes.append([-v for v in m])
         coef.append(c.conjugate())
     return np.asarray(modes, dtype=np.int64), np.asarray(coef, dtype=np.complex128)
+
+
+def warmstart_features(eps, phases, width: int = 64) -> np.ndarray:
+    """Inputs of the warm-start network for potentials eps * sum_j cos(y_j + phi_j).
+
+    Row per problem: [eps/10, log10(eps), sqrt(eps/10), cos phi_1..4, sin phi_1..4],
+    zero-padded to `width` columns. Most of the phase dependence is removed before the
+    network by a diagonal unitary on the coefficients (exact for grid-lattice phases); the
+    network learns the rest.
+    """
+    eps = np.atleast_1d(np.asarray(eps, dtype=np.float64))
+    phases = np.atleast_2d(np.asarray(phases, dtype=np.float64))
+    q = phases.shape[1]
+    f = np.zeros((eps.size, width), dtype=np.float32)
+    f[:, 0] = eps / 10.0
+    f[:, 1] = np.log10(eps)
+    f[:, 2] = np.sqrt(eps / 10.0)
+    f[:, 3:3 + q] = np.cos(phases)
+    f[:, 3 + q:3 + 2 * q] = np.sin(phases)
+    return f
