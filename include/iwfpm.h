@@ -252,6 +252,21 @@ iwf_status iwf_ws_phase(const iwf_plan* plan, int nprob, int nvec, const double*
 iwf_status iwf_apply_profile(iwf_plan* plan, int precision, const void* psi, void* hpsi,
                              int nvec, void* stream, double* pass_ms, int* launches);
 
+/*
+ * Apply schedule autotuner. Times iwf_apply on an nvec block (scratch buffers allocated and
+ * freed by the call) for every candidate schedule -- threads per CTA {128, 256}, shared-
+ * memory tile budget {24, 48, 96, 160} KB, L2 chunk of vectors between passes {24, 48, 96}
+ * MB -- and keeps the fastest for this plan and precision. Host outputs (may be NULL):
+ * *best_ms per apply, best[3] = {threads, tile_kb, chunk_mb}. Needs a potential. Results
+ * are identical for every schedule up to floating-point summation order; synchronises.
+ */
+iwf_status iwf_plan_autotune(iwf_plan* plan, int precision, int nvec, double* best_ms,
+                             int* best, void* stream);
+
+/* Set the apply schedule directly (threads 128 or 256, tile_kb 8..200, chunk_mb >= 1). */
+iwf_status iwf_plan_set_schedule(iwf_plan* plan, int precision, int threads, int tile_kb,
+                                 int chunk_mb);
+
 /* Number of kernels this library has launched in this process (all devices, all plans). */
 long long iwf_kernel_launches(void);
 

@@ -125,6 +125,21 @@ class Plan:
                                         self._stream(stream)), "iwf_apply")
         return out
 
+    def autotune(self, precision="f64", nvec=16, stream=None):
+        """iwf_plan_autotune: returns (ms per apply, (threads, tile_kb, chunk_mb))."""
+        ms = C.c_double()
+        best = (C.c_int * 3)()
+        prec = self._c.IWF_PREC_F64 if precision == "f64" else self._c.IWF_PREC_C64
+        self._c.check(self._c.iwf_plan_autotune(self.handle, prec, int(nvec), C.byref(ms), best,
+                                                self._stream(stream)), "iwf_plan_autotune")
+        return float(ms.value), tuple(int(v) for v in best)
+
+    def set_schedule(self, precision, threads, tile_kb, chunk_mb):
+        prec = self._c.IWF_PREC_F64 if precision == "f64" else self._c.IWF_PREC_C64
+        self._c.check(self._c.iwf_plan_set_schedule(self.handle, prec, int(threads),
+                                                    int(tile_kb), int(chunk_mb)),
+                      "iwf_plan_set_schedule")
+
     def apply_profile(self, psi, out, stream=None):
         """iwf_apply_profile: same result as apply(); returns (pass_ms[3], launches[3])."""
         nvec = self._check_block(psi)

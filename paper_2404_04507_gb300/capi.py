@@ -68,6 +68,8 @@ _PROTOS = {
                                C.POINTER(_i)]),
     "iwf_kernel_launches": (_ll, []),
     "iwf_apply_noalloc": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
+    "iwf_plan_autotune": (_i, [_vp, _i, _i, C.POINTER(C.c_double), C.POINTER(_i), _vp]),
+    "iwf_plan_set_schedule": (_i, [_vp, _i, _i, _i, _i]),
     "iwf_eigensolve": (_i, [_vp, C.POINTER(iwf_solve_opts), _vp, C.POINTER(C.c_double), _vp,
                             C.POINTER(C.c_double), C.POINTER(iwf_solve_info), _vp]),
     "iwf_batch_eigensolve": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(C.c_double),

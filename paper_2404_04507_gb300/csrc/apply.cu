@@ -267,13 +267,10 @@ iwf_status init_twiddles(int device) {
   return IWF_OK;
 }
 
+// Choose C (inner chunk) and Ot (outer indices) for a group pass within tile_kb of smem.
 template <typename T>
-size_t tile_elems_budget() { return (size_t)(160 * 1024) / sizeof(typename Vec2<T>::type); }
-
-// Choose C (inner chunk) and Ot (outer indices) for a group pass.
-template <typename T>
-void choose_tile(PassArgs& a) {
-  const size_t budget = tile_elems_budget<T>() * 32 / 33;  // room for padding
+void choose_tile(PassArgs& a, int tile_kb) {
+  const size_t budget = (size_t)tile_kb * 1024 / sizeof(typename Vec2<T>::type) * 32 / 33;
   if (a.inner == 1) {
     a.C = 1;
     long long ot = (long long)(budget / a.M);
@@ -296,7 +293,7 @@ void choose_tile(PassArgs& a) {
 }
 
 template <typename T, int KIND>
-iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer) {
+iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer, int threads) {
   const size_t elems = (size_t)a.Ot * a.M * a.C;
   const size_t bytes = (elems + elems / 32 + 1) * sizeof(typename Vec2<T>::type);
   static bool attr_set[2][3] = {};
@@ -309,7 +306,7 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
   const long long tiles = ((a.outer + a.Ot - 1) / a.Ot) * a.tiles_inner;
   dim3 grid((unsigned)tiles, (unsigned)nvec);
   if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
-  pass_kernel<T, KIND><<<grid, kThreads, bytes, stream>>>(a);
+  pass_kernel<T, KIND><<<grid, threads, bytes, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   if (timer) {
@@ -330,9 +327,11 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
   using V2 = typename Vec2<T>::type;
   const Geom& g = p->g;
   const int d = g.d, n = g.n;
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  const int threads = p->tune_threads[ti], tile_kb = p->tune_tile_kb[ti];
   // chunk of vectors whose intermediate block fits comfortably in L2
   const size_t vbytes = (size_t)g.N * sizeof(V2);
-  int chunk = (int)((size_t)(48u << 20) / vbytes);
+  int chunk = (int)(((size_t)p->tune_chunk_mb[ti] << 20) / vbytes);
   if (chunk < 1) chunk = 1;
   if (chunk > nvec) chunk = nvec;
   if (chunk > 65535) chunk = 65535;
@@ -373,7 +372,7 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     int s = 1;
     for (int j = d - 1; j >= 0; --j) { A.grp.gs[j] = s; s *= g.lens[j]; }
   }
-  choose_tile<T>(A);
+  choose_tile<T>(A, tile_kb);
 
   PassArgs B{};
   B.g = g; B.lo = p->d_lo; B.ld = g.N; B.pot = pot;
@@ -385,7 +384,7 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     int s = 1;
     for (int j = n - d - 1; j >= 0; --j) { B.grp.gs[j] = s; s *= g.lens[d + j]; }
   }
-  choose_tile<T>(B);
+  choose_tile<T>(B, tile_kb);
 
   PassArgs Cp = A;
   Cp.lam = sizeof(T) == 8 ? (const void*)p->d_lam64 : (const void*)p->d_lam32;
@@ -397,11 +396,11 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     V2* wk = reinterpret_cast<V2*>(work);
     A.vec_base = v0; B.vec_base = v0; Cp.vec_base = v0;
     A.in = in; A.out = wk;
-    IWF_TRY((launch_pass<T, 0>(A, nv, stream, timer)));
+    IWF_TRY((launch_pass<T, 0>(A, nv, stream, timer, threads)));
     B.in = wk; B.out = wk;
-    IWF_TRY((launch_pass<T, 1>(B, nv, stream, timer)));
+    IWF_TRY((launch_pass<T, 1>(B, nv, stream, timer, threads)));
     Cp.in = wk; Cp.out = out; Cp.psi = in;
-    IWF_TRY((launch_pass<T, 2>(Cp, nv, stream, timer)));
+    IWF_TRY((launch_pass<T, 2>(Cp, nv, stream, timer, threads)));
   }
   return IWF_OK;
 }
@@ -429,6 +428,67 @@ iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, i
   if (precision == IWF_PREC_C64)
     return apply_typed<float>(p, psi, hpsi, nvec, stream, timer, nullptr, 0, batch);
   return fail(IWF_ERR_ARG, "iwf_apply: unknown precision");
+}
+
+// ---------------------------------------------------------------------------------------
+// Schedule autotuner: time the apply of an nvec block for every candidate (threads per CTA,
+// shared-memory tile budget, L2 chunk) and keep the fastest for this plan and precision.
+iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, int* best,
+                         cudaStream_t stream) {
+  if (precision != IWF_PREC_F64 && precision != IWF_PREC_C64)
+    return fail(IWF_ERR_ARG, "iwf_plan_autotune: unknown precision");
+  if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_plan_autotune: no potential set");
+  if (nvec < 1 || nvec > 65535) return fail(IWF_ERR_ARG, "iwf_plan_autotune: bad nvec");
+  const int ti = precision == IWF_PREC_F64 ? 0 : 1;
+  const size_t elt = precision == IWF_PREC_F64 ? 16 : 8;
+  const size_t bytes = (size_t)p->g.N * nvec * elt;
+  void *x = nullptr, *y = nullptr;
+  if (cudaMalloc(&x, bytes) != cudaSuccess) return fail(IWF_ERR_ALLOC, "autotune buffers");
+  if (cudaMalloc(&y, bytes) != cudaSuccess) { cudaFree(x); return fail(IWF_ERR_ALLOC, "autotune buffers"); }
+  cudaMemsetAsync(x, 0, bytes, stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int threads[] = {128, 256};
+  const int tiles[] = {24, 48, 96, 160};
+  const int chunks[] = {24, 48, 96};
+  double best_t = 1e30;
+  int bt = p->tune_threads[ti], bk = p->tune_tile_kb[ti], bc = p->tune_chunk_mb[ti];
+  iwf_status st = IWF_OK;
+  for (int th : threads)
+    for (int tk : tiles)
+      for (int ch : chunks) {
+        if (st != IWF_OK) break;
+        p->tune_threads[ti] = th; p->tune_tile_kb[ti] = tk; p->tune_chunk_mb[ti] = ch;
+        st = apply_impl(p, precision, x, y, nvec, stream);           // warm-up (and workspace)
+        if (st != IWF_OK) break;
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 3 && st == IWF_OK; ++r) st = apply_impl(p, precision, x, y, nvec, stream);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(IWF_ERR_CUDA, "autotune timing"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / 3 < best_t) { best_t = ms / 3; bt = th; bk = tk; bc = ch; }
+      }
+  p->tune_threads[ti] = bt; p->tune_tile_kb[ti] = bk; p->tune_chunk_mb[ti] = bc;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (st != IWF_OK) return st;
+  if (best_ms) *best_ms = best_t;
+  if (best) { best[0] = bt; best[1] = bk; best[2] = bc; }
+  return IWF_OK;
+}
+
+iwf_status set_schedule_impl(iwf_plan* p, int precision, int threads, int tile_kb, int chunk_mb) {
+  if (precision != IWF_PREC_F64 && precision != IWF_PREC_C64)
+    return fail(IWF_ERR_ARG, "iwf_plan_set_schedule: unknown precision");
+  if ((threads != 128 && threads != 256) || tile_kb < 8 || tile_kb > 200 || chunk_mb < 1)
+    return fail(IWF_ERR_ARG, "iwf_plan_set_schedule: threads 128 or 256, tile_kb 8..200, chunk_mb >= 1");
+  const int ti = precision == IWF_PREC_F64 ? 0 : 1;
+  p->tune_threads[ti] = threads; p->tune_tile_kb[ti] = tile_kb; p->tune_chunk_mb[ti] = chunk_mb;
+  return IWF_OK;
 }
 
 // ---------------------------------------------------------------------------------------

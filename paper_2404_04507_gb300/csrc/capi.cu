@@ -236,6 +236,20 @@ iwf_status iwf_apply_profile(iwf_plan* p, int precision, const void* psi, void* 
 
 long long iwf_kernel_launches(void) { return launch_count(); }
 
+iwf_status iwf_plan_autotune(iwf_plan* p, int precision, int nvec, double* best_ms, int* best,
+                             void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_autotune: NULL plan");
+  DeviceGuard guard(p->device);
+  return autotune_impl(p, precision, nvec, best_ms, best, (cudaStream_t)stream);
+}
+
+iwf_status iwf_plan_set_schedule(iwf_plan* p, int precision, int threads, int tile_kb,
+                                 int chunk_mb) {
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_set_schedule: NULL plan");
+  return set_schedule_impl(p, precision, threads, tile_kb, chunk_mb);
+}
+
 iwf_status iwf_batch_eigensolve(iwf_plan* p, int nprob, const int* nmodes, const int* m,
                                 const double* re, const double* im, const iwf_solve_opts* opts,
                                 const void* X0, double* evals, void* evecs, double* resid,

@@ -108,6 +108,10 @@ struct iwf_plan {
   // workspace for the apply
   void* d_work = nullptr;
   size_t work_bytes = 0;
+  // apply launch schedule per precision (0: FP64, 1: complex64), set by iwf_plan_autotune
+  int tune_threads[2] = {256, 256};
+  int tune_tile_kb[2] = {160, 160};
+  int tune_chunk_mb[2] = {48, 48};
 };
 
 namespace iwf {
@@ -129,6 +133,9 @@ iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, cons
                                  const double* re, const double* im, const iwf_solve_opts* o,
                                  const void* X0, double* evals, void* evecs, double* resid,
                                  int* iters, iwf_solve_info* info, cudaStream_t st);
+iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, int* best,
+                         cudaStream_t stream);
+iwf_status set_schedule_impl(iwf_plan* p, int precision, int threads, int tile_kb, int chunk_mb);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties

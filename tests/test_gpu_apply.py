@@ -145,3 +145,31 @@ def test_errors_are_reported(iwf):
     with pytest.raises(capi.IwfError) as e:
         plan.set_potential(np.array([[1, 0]]), np.array([1.0 + 0j]))   # not real
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("sched", [(128, 24, 24), (128, 96, 48), (256, 48, 96), (256, 160, 48)])
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_every_schedule_gives_the_same_operator(iwf, sched, prec):
+    pb = PROBS["moire_ragged"]
+    plan = _plan(iwf, pb)
+    plan.set_schedule(prec, *sched)
+    win, Vg = _oracle(pb)
+    X = W.random_block(win.N, 5, seed=12)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    Xin = X.astype(np.complex64).astype(np.complex128) if prec == "c64" else X
+    got = _gpu_apply(plan, Xin, dtype)
+    want = O.apply_stencil(win, Vg, Xin)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+def test_autotune_picks_a_valid_schedule(iwf):
+    pb = W.config_moire(eps=0.5, K=8, L=8)
+    plan = _plan(iwf, pb)
+    ms, best = plan.autotune("c64", nvec=4)
+    assert ms > 0 and best[0] in (128, 256) and best[1] in (24, 48, 96, 160)
+    win, Vg = _oracle(pb)
+    X = W.random_block(win.N, 2, seed=1).astype(np.complex64).astype(np.complex128)
+    got = _gpu_apply(plan, X, torch.complex64)
+    want = O.apply_stencil(win, Vg, X)
+    assert np.max(np.abs(got - want)) <= TOL32 * np.max(np.abs(want))
