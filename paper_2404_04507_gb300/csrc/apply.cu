@@ -49,7 +49,8 @@ struct PassArgs {
   GroupDesc grp;
   int M;                    // points of the group (product of len)
   long long inner;          // points of all faster axes
-  int C;                    // inner chunk per tile
+  int C;                    // inner chunk per tile (a power of two)
+  int lc;                   // log2(C)
   int Ot;                   // outer indices per tile
   long long outer;          // number of outer indices
   long long tiles_inner;    // inner chunks per outer index
@@ -60,6 +61,7 @@ struct PassArgs {
   const int* lo;            // MII x d
   PotDev pot;               // pass B only (tables); all passes (batch skipping)
   long long ld;             // element stride between vectors (= N)
+  int tile_bytes;           // shared-memory bytes of the tile (pass B's V tables follow it)
   int vec_base;             // index of the launch's first vector in the whole block
 };
 
@@ -80,24 +82,26 @@ template <typename T, int LEN, int S, bool ROLL_LOAD, bool ROLL_STORE>
 __device__ void axis_dft(typename Vec2<T>::type* tile, const PassArgs& a, int ax, long long o0,
                          const int* s_off) {
   using V2 = typename Vec2<T>::type;
-  const int C = a.C, M = a.M;
+  const int lc = a.lc, M = a.M;
   const int gs = a.grp.gs[ax];
-  const int per_o = (M / LEN) * C;
+  const int step = gs << lc;                       // tile distance between pencil elements
+  const int per_o = (M / LEN) << lc;
   const int npen = per_o * a.Ot;
   for (int p = threadIdx.x; p < npen; p += blockDim.x) {
     const int ot = p / per_o;
     const int rem = p - ot * per_o;
-    const int c = rem % C;
-    const int rest = rem / C;
-    const int g0 = (rest / gs) * gs * LEN + rest % gs;
-    const int base = ot * M * C;
+    const int c = rem & ((1 << lc) - 1);
+    const int rest = rem >> lc;
+    const int q = rest / gs;
+    const int g0 = q * gs * LEN + (rest - q * gs);
+    const int base = ((ot * M + g0) << lc) + c;
     const int off = (ROLL_LOAD || ROLL_STORE) ? s_off[ot * IWF_MAX_N + ax] : 0;
     T xr[LEN], xi[LEN];
 #pragma unroll
     for (int i = 0; i < LEN; ++i) {
       int src = i;
       if (ROLL_LOAD) { src = i + off; if (src >= LEN) src -= LEN; }
-      const V2 v = tile[padx(base + (g0 + src * gs) * C + c)];
+      const V2 v = tile[padx(base + src * step)];
       xr[i] = v.x; xi[i] = v.y;
     }
     Dft<LEN, S, T>::run(xr, xi);
@@ -106,7 +110,7 @@ __device__ void axis_dft(typename Vec2<T>::type* tile, const PassArgs& a, int ax
       int dst = i;
       if (ROLL_STORE) { dst = i + off; if (dst >= LEN) dst -= LEN; }
       V2 v; v.x = xr[i]; v.y = xi[i];
-      tile[padx(base + (g0 + dst * gs) * C + c)] = v;
+      tile[padx(base + dst * step)] = v;
     }
   }
 }
@@ -159,15 +163,31 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
     const int ot = t / a.grp.ng, ax = t % a.grp.ng;
     s_off[ot * IWF_MAX_N + ax] = roll_off(a, ax, o0 + ot);
   }
-  // stage the tile: rows of C contiguous elements, one row per (outer, group point)
-  const int C = a.C, M = a.M;
+  // stage the tile: rows of C contiguous elements, one row per (outer, group point);
+  // element e of the tile sits at (e >> lc) * inner + (e & (C-1)) from the tile's origin
+  const int C = a.C, M = a.M, lc = a.lc;
   const int nel = Ot * M * C;
-  for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-    const int c = e % C;
-    const int gm = e / C;  // ot * M + g
-    const size_t gi = (size_t)(o0 * M + gm) * a.inner + c0 + c;
-    tile[padx(e)] = in[gi];
+  const size_t org = (size_t)o0 * M * a.inner + c0;
+  const V2* tin = in + org;
+  const bool contig = a.inner == C;                // the whole tile is one contiguous run
+  auto gidx = [&](int e) -> size_t {
+    return contig ? (size_t)e : (size_t)(e >> lc) * a.inner + (e & (C - 1));
+  };
+  // complex float: two neighbours of a row (or of a contiguous tile) move as one 16-byte word
+  const bool pairs = sizeof(T) == 4 && (contig || C >= 2) && (nel % 2 == 0);
+  bool staged = false;
+  if constexpr (sizeof(T) == 4) {
+    if (pairs) {
+      for (int e = 2 * threadIdx.x; e < nel; e += 2 * blockDim.x) {
+        const float4 w = *reinterpret_cast<const float4*>(tin + gidx(e));
+        tile[padx(e)] = make_float2(w.x, w.y);
+        tile[padx(e + 1)] = make_float2(w.z, w.w);
+      }
+      staged = true;
+    }
   }
+  if (!staged)
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) tile[padx(e)] = tin[gidx(e)];
   __syncthreads();
 
   if (KIND == 0) {
@@ -180,32 +200,47 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
       axis_dispatch<T, +1, true, false>(tile, a, ax, o0, s_off);
       __syncthreads();
     }
-    // multiply by V(y_l)/N: l_II from the group point, l_I from the inner index
-    const long long tbase = (long long)prob * a.pot.tab_stride;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-      const int c = e % C;
-      const int g = (e / C) % M;
-      T v;
-      if (a.pot.kind == 1) {
-        v = pot_const<T>(a.pot);
+    // multiply by V(y_l)/N: l_II from the group point, l_I from the inner index. With
+    // per-axis tables V = [const + sum over k_I axes] + [sum over k_II axes]; both parts are
+    // tabulated once per tile (vI over the C inner indices, vII over the M group points).
+    if (a.pot.kind == 1) {
+      T* vII = reinterpret_cast<T*>(smem_raw + a.tile_bytes);
+      T* vI = vII + M;
+      const long long tbase = (long long)prob * a.pot.tab_stride;
+      for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        T v = pot_const<T>(a.pot);
         long long rem = c0 + c;              // inner index -> l_I coordinates (C order)
         for (int j = a.g.d - 1; j >= 0; --j) {
           const int lj = (int)(rem % a.g.lens[j]);
           rem /= a.g.lens[j];
           v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[j] + lj);
         }
+        vI[c] = v;
+      }
+      for (int g = threadIdx.x; g < M; g += blockDim.x) {
+        T v = T(0);
         int gr = g;                          // group point -> l_II coordinates
         for (int ax = a.grp.ng - 1; ax >= 0; --ax) {
           const int lj = gr % a.grp.len[ax];
           gr /= a.grp.len[ax];
           v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[a.g.d + ax] + lj);
         }
-      } else {
-        v = pot_grid<T>(a.pot, (long long)g * a.inner + c0 + c);
+        vII[g] = v;
       }
-      V2 x = tile[padx(e)];
-      x.x *= v; x.y *= v;
-      tile[padx(e)] = x;
+      __syncthreads();
+      for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const T v = vI[e & (C - 1)] + vII[e >> lc];
+        V2 x = tile[padx(e)];
+        x.x *= v; x.y *= v;
+        tile[padx(e)] = x;
+      }
+    } else {
+      for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const T v = pot_grid<T>(a.pot, (long long)(e >> lc) * a.inner + c0 + (e & (C - 1)));
+        V2 x = tile[padx(e)];
+        x.x *= v; x.y *= v;
+        tile[padx(e)] = x;
+      }
     }
     __syncthreads();
     for (int ax = 0; ax < a.grp.ng; ++ax) {
@@ -219,26 +254,31 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
     }
   }
 
+  V2* tout = out + org;
   if (KIND == 2) {
-    const V2* psi = reinterpret_cast<const V2*>(a.psi) + (size_t)vec * a.ld;
-    const T* lam = reinterpret_cast<const T*>(a.lam);
+    const V2* psi = reinterpret_cast<const V2*>(a.psi) + (size_t)vec * a.ld + org;
+    const T* lam = reinterpret_cast<const T*>(a.lam) + org;
     for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-      const int c = e % C;
-      const int gm = e / C;
-      const size_t gi = (size_t)(o0 * M + gm) * a.inner + c0 + c;
+      const size_t gi = gidx(e);
       const V2 x = tile[padx(e)];
       const V2 p = psi[gi];
       const T l = lam[gi];
       V2 r; r.x = x.x + l * p.x; r.y = x.y + l * p.y;
-      out[gi] = r;
+      tout[gi] = r;
     }
   } else {
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-      const int c = e % C;
-      const int gm = e / C;
-      const size_t gi = (size_t)(o0 * M + gm) * a.inner + c0 + c;
-      out[gi] = tile[padx(e)];
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (pairs) {
+        for (int e = 2 * threadIdx.x; e < nel; e += 2 * blockDim.x) {
+          const V2 u0 = tile[padx(e)], u1 = tile[padx(e + 1)];
+          *reinterpret_cast<float4*>(tout + gidx(e)) = make_float4(u0.x, u0.y, u1.x, u1.y);
+        }
+        done = true;
+      }
     }
+    if (!done)
+      for (int e = threadIdx.x; e < nel; e += blockDim.x) tout[gidx(e)] = tile[padx(e)];
   }
 }
 
@@ -270,7 +310,10 @@ iwf_status init_twiddles(int device) {
 // Choose C (inner chunk) and Ot (outer indices) for a group pass within tile_kb of smem.
 template <typename T>
 void choose_tile(PassArgs& a, int tile_kb) {
-  const size_t budget = (size_t)tile_kb * 1024 / sizeof(typename Vec2<T>::type) * 32 / 33;
+  // pass B (inner > 1) also keeps its group's V table (M values) next to the tile
+  long long kb = (long long)tile_kb * 1024 - (a.inner > 1 ? (long long)a.M * sizeof(T) : 0);
+  if (kb < 0) kb = 0;
+  const size_t budget = (size_t)kb / sizeof(typename Vec2<T>::type) * 32 / 33;
   if (a.inner == 1) {
     a.C = 1;
     long long ot = (long long)(budget / a.M);
@@ -289,13 +332,18 @@ void choose_tile(PassArgs& a, int tile_kb) {
     while (p * 2 <= c && a.inner % (p * 2) == 0) p *= 2;
     a.C = (int)p;
   }
+  a.lc = 0;
+  while ((1 << a.lc) < a.C) ++a.lc;
   a.tiles_inner = a.inner / a.C;
 }
 
 template <typename T, int KIND>
 iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer, int threads) {
   const size_t elems = (size_t)a.Ot * a.M * a.C;
-  const size_t bytes = (elems + elems / 32 + 1) * sizeof(typename Vec2<T>::type);
+  const size_t tbytes = ((elems + elems / 32 + 1) * sizeof(typename Vec2<T>::type) + 15) / 16 * 16;
+  a.tile_bytes = (int)tbytes;
+  const size_t bytes = tbytes + (KIND == 1 ? (size_t)(a.M + a.C) * sizeof(T) : 0);
+  if (bytes > 200 * 1024) return fail(IWF_ERR_UNSUPPORTED, "apply: tile exceeds shared memory");
   static bool attr_set[2][3] = {};
   const int ti = sizeof(T) == 8 ? 0 : 1;
   if (!attr_set[ti][KIND]) {
