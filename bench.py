@@ -41,6 +41,9 @@ EPS = 0.5
 # = 1.26e12, i.e. the nominal 1.25 TFLOP/s. The FP64 passes are bound by it, not by HBM.
 FP64_PEAK_TFLOPS = 1.25
 PROFILE_FILE = os.path.join(ROOT, "profiles", "apply_pass_b_moire32_f64.txt")
+# the schedule the autotuner picks for this workload on a GB300 (threads, tile KB, chunk MB);
+# --fixed-schedule applies it without tuning, so profiler runs see only the timed kernels
+FIXED_SCHEDULE = {"f64": (128, 96, 96), "c64": (128, 48, 96)}
 
 
 def _dist():
@@ -253,6 +256,12 @@ def run_ours(args):
     # schedule autotuner (outside the timed region): threads, smem tile, L2 chunk per precision
     tune = {}
     for prec in ("f64", "c64"):
+        if args.fixed_schedule:
+            sched = FIXED_SCHEDULE[prec]
+            plan.set_schedule(prec, *sched)
+            tune[prec] = {"threads": sched[0], "tile_kb": sched[1], "chunk_mb": sched[2],
+                          "ms": None, "fixed": True}
+            continue
         ms_t, best = plan.autotune(prec, nvec=NVEC)
         tune[prec] = {"threads": best[0], "tile_kb": best[1], "chunk_mb": best[2],
                       "ms": round(ms_t, 4)}
@@ -394,6 +403,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true",
                     help="skip the time-to-eigenpairs measurement (IWFPM vs PM)")
+    ap.add_argument("--fixed-schedule", action="store_true",
+                    help="use the known tuned apply schedule instead of autotuning")
     ap.add_argument("--solve-only", action="store_true",
                     help="run one eigensolve and print its timing (profiling aid)")
     ap.add_argument("--solve-run", default="iwfpm_f64", choices=[r[0] for r in SOLVE_RUNS])
