@@ -253,19 +253,43 @@ iwf_status iwf_apply_profile(iwf_plan* plan, int precision, const void* psi, voi
                              int nvec, void* stream, double* pass_ms, int* launches);
 
 /*
+ * Apply kernels. Both compute the same three passes (Sec. 4.1); they differ in how a pass
+ * moves data:
+ *   IWF_PATH_TILED   stages shared-memory tiles and runs every axis of a group on them; any
+ *                    geometry (axis lengths 2..32);
+ *   IWF_PATH_PENCIL  keeps one pencil per thread in registers, loaded from and stored to
+ *                    global memory directly, with one shared-memory transpose per pass;
+ *                    needs n = 4, d = 2 with 2K_1 = 2K_2 and 2L_1 = 2L_2, each 16 or 32;
+ *   IWF_PATH_AUTO    the pencil path where the geometry allows it, else the tiled path.
+ */
+enum { IWF_PATH_AUTO = 0, IWF_PATH_TILED = 1, IWF_PATH_PENCIL = 2 };
+
+/*
  * Apply schedule autotuner. Times iwf_apply on an nvec block (scratch buffers allocated and
- * freed by the call) for every candidate schedule -- threads per CTA {128, 256}, shared-
- * memory tile budget {24, 48, 96, 160} KB, L2 chunk of vectors between passes {24, 48, 96}
- * MB -- and keeps the fastest for this plan and precision. Host outputs (may be NULL):
- * *best_ms per apply, best[3] = {threads, tile_kb, chunk_mb}. Needs a potential. Results
- * are identical for every schedule up to floating-point summation order; synchronises.
+ * freed by the call) for every candidate schedule and keeps the fastest for this plan and
+ * precision. Candidates: the tiled path with threads per CTA {128, 256}, shared-memory tile
+ * budget {24, 48, 96, 160} KB and L2 chunk of vectors between passes {24, 48, 96} MB; where
+ * the geometry allows it, the pencil path with chunks {12, 24, 48, 96} MB. Host outputs
+ * (may be NULL): *best_ms per apply, best[3] = {threads, tile_kb, chunk_mb} (threads and
+ * tile_kb are 0 when the pencil path won; iwf_plan_get_schedule reports the path). Needs a
+ * potential. Results are identical for every schedule up to floating-point summation order;
+ * synchronises.
  */
 iwf_status iwf_plan_autotune(iwf_plan* plan, int precision, int nvec, double* best_ms,
                              int* best, void* stream);
 
-/* Set the apply schedule directly (threads 128 or 256, tile_kb 8..200, chunk_mb >= 1). */
+/* Set the apply schedule directly (threads 128 or 256, tile_kb 8..200, chunk_mb >= 1). The
+ * threads and tile budget are used by the tiled path, the chunk by both; the path is kept. */
 iwf_status iwf_plan_set_schedule(iwf_plan* plan, int precision, int threads, int tile_kb,
                                  int chunk_mb);
+
+/* Choose the apply kernels (IWF_PATH_*). IWF_PATH_PENCIL on a geometry it does not cover
+ * returns IWF_ERR_UNSUPPORTED and leaves the plan unchanged. */
+iwf_status iwf_plan_set_path(iwf_plan* plan, int precision, int path);
+
+/* The schedule iwf_apply will use: sched[4] = {threads, tile_kb, chunk_mb, path}, path
+ * being IWF_PATH_TILED or IWF_PATH_PENCIL (IWF_PATH_AUTO resolved for this geometry). */
+iwf_status iwf_plan_get_schedule(const iwf_plan* plan, int precision, int* sched);
 
 /* Number of kernels this library has launched in this process (all devices, all plans). */
 long long iwf_kernel_launches(void);

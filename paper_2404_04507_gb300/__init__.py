@@ -140,6 +140,24 @@ class Plan:
                                                     int(tile_kb), int(chunk_mb)),
                       "iwf_plan_set_schedule")
 
+    _PATHS = {"auto": 0, "tiled": 1, "pencil": 2}
+
+    def set_path(self, precision, path):
+        """iwf_plan_set_path: path is "auto", "tiled" or "pencil"."""
+        prec = self._c.IWF_PREC_F64 if precision == "f64" else self._c.IWF_PREC_C64
+        self._c.check(self._c.iwf_plan_set_path(self.handle, prec, self._PATHS[path]),
+                      "iwf_plan_set_path")
+
+    def schedule(self, precision):
+        """iwf_plan_get_schedule: dict with threads, tile_kb, chunk_mb and path."""
+        prec = self._c.IWF_PREC_F64 if precision == "f64" else self._c.IWF_PREC_C64
+        out = (C.c_int * 4)()
+        self._c.check(self._c.iwf_plan_get_schedule(self.handle, prec, out),
+                      "iwf_plan_get_schedule")
+        names = {1: "tiled", 2: "pencil"}
+        return {"threads": out[0], "tile_kb": out[1], "chunk_mb": out[2],
+                "path": names[out[3]]}
+
     def apply_profile(self, psi, out, stream=None):
         """iwf_apply_profile: same result as apply(); returns (pass_ms[3], launches[3])."""
         nvec = self._check_block(psi)

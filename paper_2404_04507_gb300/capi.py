@@ -19,6 +19,7 @@ STATUS = {0: "IWF_OK", -1: "IWF_ERR_ARG", -2: "IWF_ERR_SINGULAR_PI", -3: "IWF_ER
 IWF_METHOD_IWFPM, IWF_METHOD_PM = 0, 1
 IWF_SHIFT_EXACT, IWF_SHIFT_ROUND = 0, 1
 IWF_PREC_F64, IWF_PREC_C64 = 0, 1
+IWF_PATH_AUTO, IWF_PATH_TILED, IWF_PATH_PENCIL = 0, 1, 2
 
 
 class IwfError(RuntimeError):
@@ -70,6 +71,8 @@ _PROTOS = {
     "iwf_apply_noalloc": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_plan_autotune": (_i, [_vp, _i, _i, C.POINTER(C.c_double), C.POINTER(_i), _vp]),
     "iwf_plan_set_schedule": (_i, [_vp, _i, _i, _i, _i]),
+    "iwf_plan_set_path": (_i, [_vp, _i, _i]),
+    "iwf_plan_get_schedule": (_i, [_vp, _i, C.POINTER(_i)]),
     "iwf_eigensolve": (_i, [_vp, C.POINTER(iwf_solve_opts), _vp, C.POINTER(C.c_double), _vp,
                             C.POINTER(C.c_double), C.POINTER(iwf_solve_info), _vp]),
     "iwf_batch_eigensolve": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(C.c_double),

@@ -12,6 +12,12 @@
 //                         add Lambda_k psi_k.
 // Rolls are index permutations inside a pencil and cost no arithmetic. Vectors are processed
 // in chunks sized so that the intermediate block stays resident in the 129 MB L2.
+//
+// Two kernel sets implement the passes. The tiled set (pass_kernel) stages whole tiles in
+// shared memory and handles every geometry. The pencil set (pencil_*) covers two k_I and two
+// k_II axes of equal lengths 16 or 32 (the 2D moire family): one pencil per thread in
+// registers, global loads and stores straight from registers, one swizzled shared-memory
+// transpose per axis change, and for complex float a bulk-copy pipeline in pass C.
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -142,7 +148,7 @@ template <> __device__ __forceinline__ float pot_const<float>(const PotDev& p) {
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
   using V2 = typename Vec2<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   V2* tile = reinterpret_cast<V2*>(smem_raw);
   __shared__ int s_off[64 * IWF_MAX_N];
 
@@ -282,6 +288,434 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Pencil path for the common geometry of two k_I axes of length LI and two k_II axes of
+// length LII (LI, LII in {16, 32}; the 2D moire family). Every thread holds one whole
+// pencil in registers: the first axis is loaded straight from global memory (L independent
+// loads per thread, coalesced because the lanes run along the other, contiguous axis), one
+// XOR-swizzled shared-memory transpose switches to the second axis, and results leave
+// registers straight for global memory. The intermediate block uses its own slice layout:
+// position l1 * LI + l0 for the k_I grid point (l0, l1), i.e. each slice is stored
+// transposed, which makes pass A's stores and pass C's loads coalesced.
+//
+// Bank conflicts: a warp-wide access of 8-byte (16-byte) elements is served in wavefronts of
+// G = 16 (8) lanes; the swizzles make the G element indices of every wavefront distinct
+// modulo G, both when a pencil is written and when the transposed pencil is read.
+struct PencilArgs {
+  const void* in;
+  void* out;
+  const void* psi;          // pass C
+  const void* lam;          // pass C
+  const int* lo;            // MII x 2 slice bounds (passes A and C)
+  PotDev pot;               // pass B tables or grid; batch skipping in every pass
+  long long ld;             // N, elements between vectors
+  long long MI, MII;        // LI^2, LII^2
+  int vec_base;
+};
+
+template <typename T> constexpr int wave_lanes() { return sizeof(T) == 4 ? 16 : 8; }
+
+__device__ __forceinline__ bool pencil_skip(const PencilArgs& a, int vec) {
+  if (a.pot.vecs_per_prob <= 0 || !a.pot.active) return false;
+  return !a.pot.active[(a.vec_base + vec) / a.pot.vecs_per_prob];
+}
+
+__device__ __forceinline__ int roll_of(int lo, int len) {
+  int off = (-lo) % len;
+  return off < 0 ? off + len : off;
+}
+
+// Pass A (KIND 0) and pass C (KIND 2) over whole slices. A warp owns 32 / L slices; lane
+// (s, p) of it loads grid column p of slice s along axis 0, so each load instruction reads
+// whole 32-element rows of the slice (a permutation of them, because of the roll).
+template <typename T, int L, int KIND>
+__global__ void __launch_bounds__(256) pencil_ac_kernel(PencilArgs a) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int SPW = 32 / L, LL = L * L;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = lane / L, p = lane % L;
+  const long long o = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * SPW + s;
+  const int vec = blockIdx.y;
+  if (pencil_skip(a, vec)) return;
+  if (((long long)blockIdx.x * (blockDim.x >> 5) + warp) * SPW >= a.MII) return;  // whole warp idle
+  const bool valid = o < a.MII;
+  V2* S = reinterpret_cast<V2*>(smem_raw) + (size_t)threadIdx.x / L * LL;  // this slice's buffer
+  int off0 = 0, off1 = 0;
+  if (valid) { off0 = roll_of(a.lo[2 * o], L); off1 = roll_of(a.lo[2 * o + 1], L); }
+  const size_t sbase = (size_t)vec * a.ld + (size_t)o * LL;
+  T xr[L], xi[L];
+  if (KIND == 0) {
+    // window order -> grid: grid (i, p) sits at window ((i + off0) mod L, (p + off1) mod L)
+    const V2* in = reinterpret_cast<const V2*>(a.in) + sbase;
+    const int col = (p + off1) & (L - 1);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      V2 v{};
+      if (valid) v = in[((i + off0) & (L - 1)) * L + col];
+      xr[i] = v.x; xi[i] = v.y;
+    }
+    Dft<L, +1, T>::run(xr, xi);                         // along axis 0: lane p has column p
+#pragma unroll
+    for (int i = 0; i < L; ++i) { V2 v; v.x = xr[i]; v.y = xi[i]; S[i * L + (p ^ i)] = v; }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < L; ++j) { const V2 v = S[p * L + (j ^ p)]; xr[j] = v.x; xi[j] = v.y; }
+    Dft<L, +1, T>::run(xr, xi);                         // along axis 1: lane p has row l0 = p
+    if (valid) {
+      V2* out = reinterpret_cast<V2*>(a.out) + sbase;
+#pragma unroll
+      for (int j = 0; j < L; ++j) { V2 v; v.x = xr[j]; v.y = xi[j]; out[j * L + p] = v; }
+    }
+  } else {
+    const V2* in = reinterpret_cast<const V2*>(a.in) + sbase;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      V2 v{};
+      if (valid) v = in[j * L + p];
+      xr[j] = v.x; xi[j] = v.y;
+    }
+    Dft<L, -1, T>::run(xr, xi);                         // along axis 1 for row l0 = p
+#pragma unroll
+    for (int j = 0; j < L; ++j) { V2 v; v.x = xr[j]; v.y = xi[j]; S[p * L + (j ^ p)] = v; }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < L; ++i) { const V2 v = S[i * L + (p ^ i)]; xr[i] = v.x; xi[i] = v.y; }
+    Dft<L, -1, T>::run(xr, xi);                         // along axis 0 for column p
+    if (valid) {
+      // grid -> window order, + Lambda psi at the same window positions. psi and H psi never
+      // overlap (checked on the host), so the loads of a batch are all issued before its
+      // stores instead of one load round trip per element.
+      const V2* __restrict__ psi = reinterpret_cast<const V2*>(a.psi) + sbase;
+      const T* __restrict__ lam = reinterpret_cast<const T*>(a.lam) + (size_t)o * LL;
+      V2* __restrict__ out = reinterpret_cast<V2*>(a.out) + sbase;
+      const int col = (p + off1) & (L - 1);
+      constexpr int kBatch = 8;
+#pragma unroll
+      for (int i0 = 0; i0 < L; i0 += kBatch) {
+        V2 q[kBatch];
+        T l[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int w = ((i0 + u + off0) & (L - 1)) * L + col;
+          q[u] = psi[w];
+          l[u] = lam[w];
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int w = ((i0 + u + off0) & (L - 1)) * L + col;
+          V2 r; r.x = xr[i0 + u] + l[u] * q[u].x; r.y = xi[i0 + u] + l[u] * q[u].y;
+          out[w] = r;
+        }
+      }
+    }
+  }
+}
+
+// ---- asynchronous bulk copies (TMA) and mbarriers -------------------------------------
+// Every wait is bounded: after kSpinRounds unsuccessful try_wait rounds the kernel records
+// kApplyTimeout in the plan's apply error word and stops.
+constexpr long long kSpinRounds = 1LL << 20;
+constexpr int kApplyTimeout = 1;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void proxy_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// Drops a 128-byte line of scratch data from L2 without writing it back (its value becomes
+// undefined): the intermediate block is dead once pass C has read it.
+__device__ __forceinline__ void discard_l2(const void* line) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(line));
+}
+__device__ __forceinline__ void store_streaming(float2* p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of the barrier; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long r = 0; r < kSpinRounds; ++r)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Global -> shared bulk copy completing on `bar` (16-byte aligned addresses and size).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Pipelined pass C. Each warp is persistent over units of 32 / L slices of one vector (32 L
+// elements, contiguous in the intermediate block) and keeps STAGES - 1 units in flight: lane 0
+// copies unit k + STAGES - 1 into shared memory with one bulk copy while the warp transforms
+// unit k. The staged unit is read once into registers and its buffer then serves the
+// transpose; its lines are then dropped from L2 (the intermediate block is dead after this
+// pass). The unit's psi and Lambda are copied into a per-warp buffer as soon as the unit
+// starts, so that the copy overlaps the two DFTs, and H psi leaves with streaming stores. The
+// slice bounds lo of all slices sit in shared memory. Units of inactive batch problems are
+// skipped.
+//
+// Shared memory: per warp STAGES staged units and psi and Lambda of one unit, then the lo
+// table (MII x 2 ints).
+template <typename T>
+__host__ __device__ constexpr size_t pipe_warp_bytes(int L, int stages) {
+  return (size_t)stages * 32 * L * sizeof(typename Vec2<T>::type) +
+         (size_t)32 * L * (sizeof(typename Vec2<T>::type) + sizeof(T));
+}
+
+template <typename T, int L, int WARPS, int STAGES>
+__global__ void __launch_bounds__(WARPS * 32) pencil_c_pipe_kernel(PencilArgs a, int nvec,
+                                                                   int* err) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int SPW = 32 / L, LL = L * L, UNIT = 32 * L;
+  constexpr uint32_t UBYTES = UNIT * sizeof(V2), LBYTES = UNIT * sizeof(T);
+  constexpr size_t WBYTES = pipe_warp_bytes<T>(L, STAGES);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[WARPS][STAGES + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = lane / L, p = lane % L;
+  unsigned char* wbase = smem_raw + (size_t)warp * WBYTES;
+  V2* stages = reinterpret_cast<V2*>(wbase);
+  V2* psi_s = stages + STAGES * UNIT;
+  T* lam_s = reinterpret_cast<T*>(psi_s + UNIT);
+  int* lo_s = reinterpret_cast<int*>(smem_raw + (size_t)WARPS * WBYTES);
+  for (long long i = threadIdx.x; i < 2 * a.MII; i += blockDim.x) lo_s[i] = a.lo[i];
+  if (lane == 0)
+    for (int st = 0; st <= STAGES; ++st) mbar_init(smem_addr(&bars[warp][st]), 1);
+  mbar_init_fence();
+  __syncthreads();
+
+  const long long upv = a.MII / SPW;                 // units per vector
+  const long long total = upv * nvec;
+  const long long nw = (long long)gridDim.x * WARPS;
+  const long long first = (long long)blockIdx.x * WARPS + warp;
+  // j-th candidate unit of this warp, and the next candidate >= j whose problem is active
+  const auto unit_of = [&](long long j) { return first + j * nw; };
+  const auto next_active = [&](long long j) {
+    while (unit_of(j) < total && pencil_skip(a, (int)(unit_of(j) / upv))) ++j;
+    return j;
+  };
+  const auto unit_offset = [&](long long j) {
+    const long long u = unit_of(j);
+    return (size_t)(u / upv) * a.ld + (size_t)(u % upv) * UNIT;
+  };
+  const auto issue = [&](long long j, int st) {       // lane 0: unit j -> stage st
+    const uint32_t bar = smem_addr(&bars[warp][st]);
+    proxy_fence();                                     // generic accesses before the async write
+    mbar_expect_tx(bar, UBYTES);
+    bulk_load(smem_addr(stages + st * UNIT), reinterpret_cast<const V2*>(a.in) + unit_offset(j),
+              UBYTES, bar);
+  };
+
+  long long jp = next_active(0);   // next unit to prefetch
+  int kp = 0;                      // unit copies issued
+  for (; kp < STAGES - 1 && unit_of(jp) < total; ++kp) {
+    if (lane == 0) issue(jp, kp % STAGES);
+    jp = next_active(jp + 1);
+  }
+  long long jc = next_active(0);
+  int k = 0;
+  bool ok = true, psi_pending = false;
+  for (; unit_of(jc) < total; ++k, jc = next_active(jc + 1)) {
+    __syncwarp();                  // unit k - 1 is done with its stage and the psi buffer
+    if (unit_of(jp) < total) {     // refill the stage unit k - 1 used
+      if (lane == 0) issue(jp, kp % STAGES);
+      ++kp;
+      jp = next_active(jp + 1);
+    }
+    const long long u = unit_of(jc);
+    const size_t uoff = unit_offset(jc);
+    if (lane == 0) {               // psi and Lambda of this unit, consumed after the DFTs
+      const uint32_t bar = smem_addr(&bars[warp][STAGES]);
+      proxy_fence();
+      mbar_expect_tx(bar, UBYTES + LBYTES);
+      bulk_load(smem_addr(psi_s), reinterpret_cast<const V2*>(a.psi) + uoff, UBYTES, bar);
+      bulk_load(smem_addr(lam_s), reinterpret_cast<const T*>(a.lam) + (size_t)(u % upv) * UNIT,
+                LBYTES, bar);
+    }
+    psi_pending = true;
+    const int st = k % STAGES;
+    ok = mbar_wait(smem_addr(&bars[warp][st]), (uint32_t)((k / STAGES) & 1));
+    if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
+    const long long o = (u % upv) * SPW + s;          // slice of this lane
+    V2* U = stages + st * UNIT + s * LL;               // this lane's slice in the stage
+    const int off0 = roll_of(lo_s[2 * o], L), off1 = roll_of(lo_s[2 * o + 1], L);
+    T xr[L], xi[L];
+    {
+#pragma unroll
+      for (int j = 0; j < L; ++j) { const V2 v = U[j * L + p]; xr[j] = v.x; xi[j] = v.y; }
+      // the unit's intermediate values now live in registers: drop its lines from L2
+      {
+        const unsigned char* g = reinterpret_cast<const unsigned char*>(
+            reinterpret_cast<const V2*>(a.in) + uoff);
+#pragma unroll
+        for (int t = 0; t < (int)(UBYTES / (32 * 128)); ++t) discard_l2(g + (t * 32 + lane) * 128);
+      }
+      Dft<L, -1, T>::run(xr, xi);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < L; ++j) { V2 v; v.x = xr[j]; v.y = xi[j]; U[p * L + (j ^ p)] = v; }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < L; ++i) { const V2 v = U[i * L + (p ^ i)]; xr[i] = v.x; xi[i] = v.y; }
+      Dft<L, -1, T>::run(xr, xi);
+      ok = mbar_wait(smem_addr(&bars[warp][STAGES]), (uint32_t)(k & 1));
+      if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
+      psi_pending = false;
+      // grid -> window order, + Lambda psi at the same window positions
+      const V2* ps = psi_s + s * LL;
+      const T* ls = lam_s + s * LL;
+      V2* out = reinterpret_cast<V2*>(a.out) + uoff + (size_t)s * LL;
+      const int col = (p + off1) & (L - 1);
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const int w = ((i + off0) & (L - 1)) * L + col;
+        const V2 q = ps[w];
+        const T l = ls[w];
+        V2 r; r.x = xr[i] + l * q.x; r.y = xi[i] + l * q.y;
+        store_streaming(out + w, r);
+      }
+    }
+  }
+  if (!ok) {
+    // record the timeout, then give the copies still in flight a bounded time to land
+    if (lane == 0) atomicExch(err, kApplyTimeout);
+    if (psi_pending) mbar_wait(smem_addr(&bars[warp][STAGES]), (uint32_t)(k & 1));
+    for (; k < kp; ++k) mbar_wait(smem_addr(&bars[warp][k % STAGES]), (uint32_t)((k / STAGES) & 1));
+  }
+}
+
+// Swizzled column of group point (k, a) of tile column c: a ^ f(c, k), a bijection in a.
+template <int C, int G>
+__device__ __forceinline__ int pencil_sw(int a, int c, int k) {
+  if constexpr (C >= G) return a ^ (c & (G - 1));
+  else return a ^ (c * (G / C)) ^ (k & (G / C - 1));
+}
+
+// Pass B (in place) on a tile of C consecutive slice positions x all LII^2 k_II points.
+// Thread (a, c) first holds the pencil along k_II axis 0 at axis-1 window coordinate a; after
+// the transpose, thread (k, c) holds the pencil along k_II axis 1 at axis-0 grid index k.
+template <typename T, int L, int C>
+__global__ void __launch_bounds__(C * L) pencil_b_kernel(PencilArgs a) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int LL = L * L, H = L / 2, G = wave_lanes<T>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  V2* S = reinterpret_cast<V2*>(smem_raw);
+  T* vI = reinterpret_cast<T*>(S + C * LL);   // C slice positions
+  T* v0 = vI + C;                             // k_II axis 0 table (L)
+  T* v1 = v0 + L;                             // k_II axis 1 table (L)
+  const int c = threadIdx.x % C, ta = threadIdx.x / C;
+  const long long c0 = (long long)blockIdx.x * C;
+  const int vec = blockIdx.y;
+  if (pencil_skip(a, vec)) return;
+  const int prob = a.pot.vecs_per_prob > 0 ? (a.vec_base + vec) / a.pot.vecs_per_prob : 0;
+  const int LI = a.MI == 256 ? 16 : 32;
+  if (a.pot.kind == 1) {
+    const long long tb = (long long)prob * a.pot.tab_stride;
+    if (threadIdx.x < C) {
+      const int pos = (int)(c0 + threadIdx.x);      // slice layout: pos = l1 * LI + l0
+      vI[threadIdx.x] = pot_const<T>(a.pot) + pot_tab<T>(a.pot, tb + a.pot.tab_off[0] + pos % LI) +
+                        pot_tab<T>(a.pot, tb + a.pot.tab_off[1] + pos / LI);
+    } else if (threadIdx.x < C + L) {
+      const int l = threadIdx.x - C;
+      v0[l] = pot_tab<T>(a.pot, tb + a.pot.tab_off[2] + l);
+    } else if (threadIdx.x < C + 2 * L) {
+      const int l = threadIdx.x - C - L;
+      v1[l] = pot_tab<T>(a.pot, tb + a.pot.tab_off[3] + l);
+    }
+  }
+  // in place (a.in == a.out): every load of the tile precedes the first barrier, every store
+  // follows the second
+  V2* col = reinterpret_cast<V2*>(a.out) + (size_t)vec * a.ld + c0 + c + (size_t)ta * a.MI;
+  const int rstride = L * (int)a.MI;              // k_II axis 0 stride (N < 2^31 on this path)
+  // Shared-memory indices. Element (k, a) of column c sits at c*LL + k*L + (a ^ f(c, k)),
+  // f = pencil_sw(0, c, k). Both index families below are one XOR with an immediate on a
+  // thread constant; the constants are made opaque before each loop so that the compiler
+  // recomputes the 32 indices instead of keeping them live across the DFTs.
+  constexpr int M = (C >= G) ? 0 : G / C - 1;     // bits of k that enter f
+  int t0 = c * LL + pencil_sw<C, G>(ta, c, 0);     // (i, ta): (t0 ^ (i & M)) + i * L
+  T xr[L], xi[L];
+  // grid index i along k_II axis 0 sits at window row (i + L/2) mod L (roll by L_j)
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const V2 v = col[((i + H) & (L - 1)) * rstride];
+    xr[i] = v.x; xi[i] = v.y;
+  }
+  Dft<L, +1, T>::run(xr, xi);
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    V2 v; v.x = xr[i]; v.y = xi[i];
+    S[(t0 ^ (i & M)) + i * L] = v;
+  }
+  __syncthreads();
+  const int k = ta;
+  int r1 = (c * LL + k * L) | pencil_sw<C, G>(0, c, k);   // (k, a): r1 ^ a
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const V2 v = S[r1 ^ ((j + H) & (L - 1))];
+    xr[j] = v.x; xi[j] = v.y;
+  }
+  Dft<L, +1, T>::run(xr, xi);
+  // x V(y_l) / N at l_II = (k, j) and the tile column's k_I grid point
+  if (a.pot.kind == 1) {
+    const T base = vI[c] + v0[k];
+#pragma unroll
+    for (int j = 0; j < L; ++j) { const T v = base + v1[j]; xr[j] *= v; xi[j] *= v; }
+  } else {
+    const int pos = (int)(c0 + c);
+    const long long lI = (long long)(pos % LI) * LI + pos / LI;   // natural k_I order
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      const T v = pot_grid<T>(a.pot, (long long)(k * L + j) * a.MI + lI);
+      xr[j] *= v; xi[j] *= v;
+    }
+  }
+  Dft<L, -1, T>::run(xr, xi);
+  asm volatile("" : "+r"(r1));
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    V2 v; v.x = xr[j]; v.y = xi[j];
+    S[r1 ^ ((j + H) & (L - 1))] = v;
+  }
+  __syncthreads();
+  asm volatile("" : "+r"(t0));
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const V2 v = S[(t0 ^ (i & M)) + i * L];
+    xr[i] = v.x; xi[i] = v.y;
+  }
+  Dft<L, -1, T>::run(xr, xi);
+  // make the tile pointer opaque so that the load addresses are recomputed here instead of
+  // being kept live across the DFTs
+  asm volatile("" : "+l"(col));
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    V2 v; v.x = xr[i]; v.y = xi[i];
+    col[((i + H) & (L - 1)) * rstride] = v;
+  }
+}
+
 bool g_tw_ready[64] = {};
 
 iwf_status init_twiddles(int device) {
@@ -337,6 +771,17 @@ void choose_tile(PassArgs& a, int tile_kb) {
   a.tiles_inner = a.inner / a.C;
 }
 
+// Closes the event pair opened before a launch and adds the elapsed time to pass `kind`.
+iwf_status stop_timer(PassTimer* timer, int kind, cudaStream_t stream) {
+  IWF_CUDA(cudaEventRecord(timer->ev[1], stream));
+  IWF_CUDA(cudaEventSynchronize(timer->ev[1]));
+  float ms = 0.f;
+  IWF_CUDA(cudaEventElapsedTime(&ms, timer->ev[0], timer->ev[1]));
+  timer->ms[kind] += ms;
+  timer->launches[kind] += 1;
+  return IWF_OK;
+}
+
 template <typename T, int KIND>
 iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer, int threads) {
   const size_t elems = (size_t)a.Ot * a.M * a.C;
@@ -357,15 +802,145 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
   pass_kernel<T, KIND><<<grid, threads, bytes, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
   count_launch();
-  if (timer) {
-    IWF_CUDA(cudaEventRecord(timer->ev[1], stream));
-    IWF_CUDA(cudaEventSynchronize(timer->ev[1]));
-    float ms = 0.f;
-    IWF_CUDA(cudaEventElapsedTime(&ms, timer->ev[0], timer->ev[1]));
-    timer->ms[KIND] += ms;
-    timer->launches[KIND] += 1;
+  return timer ? stop_timer(timer, KIND, stream) : IWF_OK;
+}
+
+// Pencil path: two k_I axes of one length and two k_II axes of one length, each 16 or 32.
+bool pencil_geometry(const Geom& g, int* LI, int* LII) {
+  if (g.n != 4 || g.d != 2) return false;
+  if (g.lens[0] != g.lens[1] || g.lens[2] != g.lens[3]) return false;
+  const auto ok = [](int l) { return l == 16 || l == 32; };
+  if (!ok(g.lens[0]) || !ok(g.lens[2])) return false;
+  *LI = g.lens[0];
+  *LII = g.lens[2];
+  return true;
+}
+
+// Threads of a pass A/C CTA and tile columns of a pass B CTA: 64 KB of shared memory each.
+template <typename T> constexpr int pencil_threads() { return sizeof(T) == 4 ? 256 : 128; }
+
+// Raises the kernel's dynamic shared-memory limit on the current device to `bytes` when the
+// limit set so far (allowed[dev], per kernel and device) is smaller.
+template <typename K>
+iwf_status allow_smem(K* kernel, size_t bytes, size_t* allowed) {
+  int dev = 0;
+  IWF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(IWF_ERR_ARG, "device ordinal out of range");
+  if (allowed[dev] < bytes) {
+    IWF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    allowed[dev] = bytes;
   }
   return IWF_OK;
+}
+
+// Pipelined pass C configuration: 2 warps per CTA, 2 stages per warp (56 KB with the psi and
+// Lambda buffers for complex float at L = 32, plus the lo table).
+constexpr int kPipeWarps = 2, kPipeStages = 2;
+
+// Resident CTAs of `kernel` on the current device times its SM count, cached per device for
+// the shared-memory size it was computed with.
+struct OccCache {
+  size_t smem[64] = {};
+  int ctas[64] = {};
+};
+template <typename K>
+iwf_status persistent_ctas(K* kernel, int threads, size_t smem, OccCache* cache, int* out) {
+  int dev = 0;
+  IWF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(IWF_ERR_ARG, "device ordinal out of range");
+  if (!cache->ctas[dev] || cache->smem[dev] != smem) {
+    int per_sm = 0, sms = 0;
+    IWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    IWF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return fail(IWF_ERR_UNSUPPORTED, "pencil pass: kernel does not fit an SM");
+    cache->ctas[dev] = per_sm * sms;
+    cache->smem[dev] = smem;
+  }
+  *out = cache->ctas[dev];
+  return IWF_OK;
+}
+
+// Which pass A/C kernel runs: the pipelined one for complex-float pass C, whose psi and Lambda
+// loads it takes off the critical path; the direct one elsewhere (pass A, where it measured
+// no faster, and complex double, whose larger stages would leave too few warps for the FP64
+// units).
+template <typename T, int KIND> constexpr bool use_pipe() { return sizeof(T) == 4 && KIND == 2; }
+
+template <typename T, int L, int KIND>
+iwf_status launch_pencil_direct(const PencilArgs& a, int nvec, cudaStream_t stream,
+                                PassTimer* timer) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int threads = pencil_threads<T>();
+  constexpr int per_cta = threads / 32 * (32 / L);          // slices per CTA
+  const size_t smem = (size_t)threads * L * sizeof(V2);
+  static size_t allowed[64] = {};
+  IWF_TRY(allow_smem(pencil_ac_kernel<T, L, KIND>, smem, allowed));
+  dim3 grid((unsigned)((a.MII + per_cta - 1) / per_cta), (unsigned)nvec);
+  if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
+  pencil_ac_kernel<T, L, KIND><<<grid, threads, smem, stream>>>(a);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return timer ? stop_timer(timer, KIND, stream) : IWF_OK;
+}
+
+template <typename T, int L>
+iwf_status launch_pencil_c_pipe(const PencilArgs& a, int nvec, int* err, cudaStream_t stream,
+                                PassTimer* timer) {
+  constexpr int W = kPipeWarps, SPW = 32 / L;
+  const auto kernel = pencil_c_pipe_kernel<T, L, W, kPipeStages>;
+  const size_t smem = (size_t)W * pipe_warp_bytes<T>(L, kPipeStages) + 2 * a.MII * sizeof(int);
+  static size_t allowed[64] = {};
+  static OccCache occ;
+  IWF_TRY(allow_smem(kernel, smem, allowed));
+  int max_ctas = 0;
+  IWF_TRY(persistent_ctas(kernel, W * 32, smem, &occ, &max_ctas));
+  if (a.MII % SPW) return fail(IWF_ERR_UNSUPPORTED, "pencil pass: slices not a multiple of a unit");
+  const long long units = a.MII / SPW * nvec;
+  const long long want = (units + W - 1) / W;
+  const unsigned grid = (unsigned)(want < max_ctas ? want : max_ctas);
+  if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
+  kernel<<<grid, W * 32, smem, stream>>>(a, nvec, err);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return timer ? stop_timer(timer, 2, stream) : IWF_OK;
+}
+
+template <typename T, int L, int KIND>
+iwf_status launch_pencil_ac(const PencilArgs& a, int nvec, int* err, cudaStream_t stream,
+                            PassTimer* timer) {
+  if constexpr (use_pipe<T, KIND>()) return launch_pencil_c_pipe<T, L>(a, nvec, err, stream, timer);
+  else return launch_pencil_direct<T, L, KIND>(a, nvec, stream, timer);
+}
+
+template <typename T, int L>
+iwf_status launch_pencil_b(const PencilArgs& a, int nvec, cudaStream_t stream, PassTimer* timer) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int C = pencil_threads<T>() / L;
+  const size_t smem = (size_t)C * L * L * sizeof(V2) + (size_t)(C + 2 * L) * sizeof(T);
+  static size_t allowed[64] = {};
+  IWF_TRY(allow_smem(pencil_b_kernel<T, L, C>, smem, allowed));
+  if (a.MI % C) return fail(IWF_ERR_UNSUPPORTED, "pencil pass B: slice not a multiple of the tile");
+  dim3 grid((unsigned)(a.MI / C), (unsigned)nvec);
+  if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
+  pencil_b_kernel<T, L, C><<<grid, C * L, smem, stream>>>(a);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return timer ? stop_timer(timer, 1, stream) : IWF_OK;
+}
+
+// One chunk of vectors through the three pencil passes.
+template <typename T>
+iwf_status pencil_chunk(PencilArgs a, int LI, int LII, const void* in, void* wk, void* out,
+                        const void* lam, int nv, int* err, cudaStream_t stream, PassTimer* timer) {
+  a.in = in; a.out = wk;
+  IWF_TRY(LI == 16 ? (launch_pencil_ac<T, 16, 0>(a, nv, err, stream, timer))
+                   : (launch_pencil_ac<T, 32, 0>(a, nv, err, stream, timer)));
+  a.in = wk; a.out = wk;
+  IWF_TRY(LII == 16 ? (launch_pencil_b<T, 16>(a, nv, stream, timer))
+                    : (launch_pencil_b<T, 32>(a, nv, stream, timer)));
+  a.in = wk; a.out = out; a.psi = in; a.lam = lam;
+  return LI == 16 ? launch_pencil_ac<T, 16, 2>(a, nv, err, stream, timer)
+                  : launch_pencil_ac<T, 32, 2>(a, nv, err, stream, timer);
 }
 
 template <typename T>
@@ -437,6 +1012,21 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
   PassArgs Cp = A;
   Cp.lam = sizeof(T) == 8 ? (const void*)p->d_lam64 : (const void*)p->d_lam32;
 
+  int LI = 0, LII = 0;
+  if (p->path[ti] != IWF_PATH_TILED && pencil_geometry(g, &LI, &LII)) {
+    // pencil geometry: N = LI^2 LII^2 <= 2^20, so in-vector offsets fit in int
+    PencilArgs pa{};
+    pa.lo = p->d_lo; pa.pot = pot; pa.ld = g.N; pa.MI = g.MI; pa.MII = g.MII;
+    for (int v0 = 0; v0 < nvec; v0 += chunk) {
+      const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+      pa.vec_base = v0;
+      IWF_TRY(pencil_chunk<T>(pa, LI, LII, reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N,
+                              work, reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N, Cp.lam, nv,
+                              p->d_apply_err, stream, timer));
+    }
+    return IWF_OK;
+  }
+
   for (int v0 = 0; v0 < nvec; v0 += chunk) {
     const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
     const V2* in = reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N;
@@ -461,6 +1051,14 @@ std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// True when the nvec-vector blocks at psi and hpsi share any byte.
+static bool blocks_overlap(const iwf_plan* p, int precision, const void* psi, const void* hpsi,
+                           int nvec) {
+  const uintptr_t bytes = (uintptr_t)p->g.N * nvec * (precision == IWF_PREC_F64 ? 16 : 8);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(psi), b = reinterpret_cast<uintptr_t>(hpsi);
+  return a < b + bytes && b < a + bytes;
+}
+
 iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                       cudaStream_t stream, PassTimer* timer, const ApplyBatch* batch) {
   if (nvec < 0) return fail(IWF_ERR_ARG, "iwf_apply: nvec < 0");
@@ -470,6 +1068,8 @@ iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, i
     return fail(IWF_ERR_ARG, "iwf_apply: vectors must be 16-byte aligned");
   if (p->pot_kind == 0 && !batch) return fail(IWF_ERR_ARG, "iwf_apply: no potential set");
   if (nvec > 65535) return fail(IWF_ERR_ARG, "iwf_apply: nvec > 65535");
+  if (blocks_overlap(p, precision, psi, hpsi, nvec))
+    return fail(IWF_ERR_ARG, "iwf_apply: psi and hpsi overlap");
   IWF_TRY(init_twiddles(p->device));
   if (precision == IWF_PREC_F64)
     return apply_typed<double>(p, psi, hpsi, nvec, stream, timer, nullptr, 0, batch);
@@ -500,32 +1100,85 @@ iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, 
   const int threads[] = {128, 256};
   const int tiles[] = {24, 48, 96, 160};
   const int chunks[] = {24, 48, 96};
+  const int pencil_chunks[] = {12, 24, 48, 96};
   double best_t = 1e30;
   int bt = p->tune_threads[ti], bk = p->tune_tile_kb[ti], bc = p->tune_chunk_mb[ti];
+  int bp = IWF_PATH_TILED;
+  const int saved_path = p->path[ti];
   iwf_status st = IWF_OK;
-  for (int th : threads)
-    for (int tk : tiles)
-      for (int ch : chunks) {
-        if (st != IWF_OK) break;
-        p->tune_threads[ti] = th; p->tune_tile_kb[ti] = tk; p->tune_chunk_mb[ti] = ch;
-        st = apply_impl(p, precision, x, y, nvec, stream);           // warm-up (and workspace)
-        if (st != IWF_OK) break;
-        cudaEventRecord(e0, stream);
-        for (int r = 0; r < 3 && st == IWF_OK; ++r) st = apply_impl(p, precision, x, y, nvec, stream);
-        cudaEventRecord(e1, stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(IWF_ERR_CUDA, "autotune timing"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms / 3 < best_t) { best_t = ms / 3; bt = th; bk = tk; bc = ch; }
-      }
+  // times one candidate (the plan already holds it); keeps it if it is the fastest so far
+  const auto trial = [&](int path, int th, int tk, int ch) {
+    if (st != IWF_OK) return;
+    p->path[ti] = path;
+    p->tune_threads[ti] = th; p->tune_tile_kb[ti] = tk; p->tune_chunk_mb[ti] = ch;
+    st = apply_impl(p, precision, x, y, nvec, stream);             // warm-up (and workspace)
+    if (st != IWF_OK) return;
+    cudaEventRecord(e0, stream);
+    for (int r = 0; r < 3 && st == IWF_OK; ++r) st = apply_impl(p, precision, x, y, nvec, stream);
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(IWF_ERR_CUDA, "autotune timing"); return; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / 3 < best_t) { best_t = ms / 3; bt = th; bk = tk; bc = ch; bp = path; }
+  };
+  if (saved_path != IWF_PATH_PENCIL)
+    for (int th : threads)
+      for (int tk : tiles)
+        for (int ch : chunks) trial(IWF_PATH_TILED, th, tk, ch);
+  int LI = 0, LII = 0;
+  if (saved_path != IWF_PATH_TILED && pencil_geometry(p->g, &LI, &LII))
+    for (int ch : pencil_chunks) trial(IWF_PATH_PENCIL, p->tune_threads[ti], p->tune_tile_kb[ti], ch);
   p->tune_threads[ti] = bt; p->tune_tile_kb[ti] = bk; p->tune_chunk_mb[ti] = bc;
+  p->path[ti] = bp;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(x);
   cudaFree(y);
-  if (st != IWF_OK) return st;
+  if (st != IWF_OK) { p->path[ti] = saved_path; return st; }
   if (best_ms) *best_ms = best_t;
-  if (best) { best[0] = bt; best[1] = bk; best[2] = bc; }
+  if (best) {
+    best[0] = bp == IWF_PATH_PENCIL ? 0 : bt;
+    best[1] = bp == IWF_PATH_PENCIL ? 0 : bk;
+    best[2] = bc;
+  }
+  return IWF_OK;
+}
+
+iwf_status check_apply_error(iwf_plan* p, cudaStream_t stream) {
+  int err = 0;
+  IWF_CUDA(cudaMemcpyAsync(&err, p->d_apply_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  IWF_CUDA(cudaStreamSynchronize(stream));
+  if (err == 0) return IWF_OK;
+  IWF_CUDA(cudaMemsetAsync(p->d_apply_err, 0, sizeof(int), stream));
+  IWF_CUDA(cudaStreamSynchronize(stream));
+  return fail(IWF_ERR_TIMEOUT, "apply: a pipelined pass gave up waiting for a bulk copy");
+}
+
+iwf_status set_path_impl(iwf_plan* p, int precision, int path) {
+  if (precision != IWF_PREC_F64 && precision != IWF_PREC_C64)
+    return fail(IWF_ERR_ARG, "iwf_plan_set_path: unknown precision");
+  if (path != IWF_PATH_AUTO && path != IWF_PATH_TILED && path != IWF_PATH_PENCIL)
+    return fail(IWF_ERR_ARG, "iwf_plan_set_path: unknown path");
+  int LI = 0, LII = 0;
+  if (path == IWF_PATH_PENCIL && !pencil_geometry(p->g, &LI, &LII))
+    return fail(IWF_ERR_UNSUPPORTED,
+                "iwf_plan_set_path: the pencil path needs n = 4, d = 2 and two equal axis "
+                "lengths per group, each 16 or 32");
+  p->path[precision == IWF_PREC_F64 ? 0 : 1] = path;
+  return IWF_OK;
+}
+
+iwf_status get_schedule_impl(const iwf_plan* p, int precision, int* sched) {
+  if (precision != IWF_PREC_F64 && precision != IWF_PREC_C64)
+    return fail(IWF_ERR_ARG, "iwf_plan_get_schedule: unknown precision");
+  if (!sched) return fail(IWF_ERR_ARG, "iwf_plan_get_schedule: NULL output");
+  const int ti = precision == IWF_PREC_F64 ? 0 : 1;
+  int LI = 0, LII = 0;
+  const bool pencil = p->path[ti] != IWF_PATH_TILED && pencil_geometry(p->g, &LI, &LII);
+  sched[0] = p->tune_threads[ti];
+  sched[1] = p->tune_tile_kb[ti];
+  sched[2] = p->tune_chunk_mb[ti];
+  sched[3] = pencil ? IWF_PATH_PENCIL : IWF_PATH_TILED;
   return IWF_OK;
 }
 
@@ -575,6 +1228,8 @@ iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void*
     return fail(IWF_ERR_ARG, "iwf_apply_noalloc: vectors must be 16-byte aligned");
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: no potential set");
   if (nvec > 65535) return fail(IWF_ERR_ARG, "iwf_apply_noalloc: nvec > 65535");
+  if (blocks_overlap(p, precision, psi, hpsi, nvec))
+    return fail(IWF_ERR_ARG, "iwf_apply_noalloc: psi and hpsi overlap");
   if (precision != IWF_PREC_F64 && precision != IWF_PREC_C64)
     return fail(IWF_ERR_ARG, "iwf_apply_noalloc: unknown precision");
   const size_t elt = precision == IWF_PREC_F64 ? 16 : 8;

@@ -134,6 +134,10 @@ iwf_status plan_create(iwf_plan** out, int d, int n, const double* P, const int*
   DeviceGuard guard(p->device);
   iwf_status st = IWF_OK;
   if (cudaMalloc((void**)&p->d_err, sizeof(int)) != cudaSuccess) st = fail(IWF_ERR_ALLOC, "cudaMalloc");
+  if (st == IWF_OK && cudaMalloc((void**)&p->d_apply_err, sizeof(int)) != cudaSuccess)
+    st = fail(IWF_ERR_ALLOC, "cudaMalloc");
+  if (st == IWF_OK && cudaMemset(p->d_apply_err, 0, sizeof(int)) != cudaSuccess)
+    st = fail(IWF_ERR_CUDA, "cudaMemset");
   if (st == IWF_OK) st = build_window_tables(p);
   if (st != IWF_OK) { iwf_plan_destroy(p); return st; }
   *out = p;
@@ -164,6 +168,7 @@ void iwf_plan_destroy(iwf_plan* p) {
   cudaFree(p->d_lam64);
   cudaFree(p->d_lam32);
   cudaFree(p->d_err);
+  cudaFree(p->d_apply_err);
   cudaFree(p->d_tab64);
   cudaFree(p->d_tab32);
   cudaFree(p->d_grid64);
@@ -227,6 +232,7 @@ iwf_status iwf_apply_profile(iwf_plan* p, int precision, const void* psi, void* 
   cudaEventDestroy(t.ev[0]);
   cudaEventDestroy(t.ev[1]);
   if (st != IWF_OK) return st;
+  IWF_TRY(check_apply_error(p, (cudaStream_t)stream));
   for (int i = 0; i < 3; ++i) {
     if (pass_ms) pass_ms[i] = t.ms[i];
     if (launches) launches[i] = t.launches[i];
@@ -248,6 +254,18 @@ iwf_status iwf_plan_set_schedule(iwf_plan* p, int precision, int threads, int ti
                                  int chunk_mb) {
   if (!p) return fail(IWF_ERR_ARG, "iwf_plan_set_schedule: NULL plan");
   return set_schedule_impl(p, precision, threads, tile_kb, chunk_mb);
+}
+
+iwf_status iwf_plan_set_path(iwf_plan* p, int precision, int path) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_set_path: NULL plan");
+  return set_path_impl(p, precision, path);
+}
+
+iwf_status iwf_plan_get_schedule(const iwf_plan* p, int precision, int* sched) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_get_schedule: NULL plan");
+  return get_schedule_impl(p, precision, sched);
 }
 
 iwf_status iwf_batch_eigensolve(iwf_plan* p, int nprob, const int* nmodes, const int* m,

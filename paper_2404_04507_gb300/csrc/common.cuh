@@ -94,6 +94,7 @@ struct iwf_plan {
   double* d_lam64 = nullptr;              // N kinetic diagonal
   float* d_lam32 = nullptr;
   int* d_err = nullptr;                   // device error word
+  int* d_apply_err = nullptr;             // set by an apply kernel whose bounded wait ran out
   // potential
   int pot_kind = 0;                       // 0 unset, 1 tables, 2 grid
   double* d_tab64 = nullptr;
@@ -112,6 +113,9 @@ struct iwf_plan {
   int tune_threads[2] = {256, 256};
   int tune_tile_kb[2] = {160, 160};
   int tune_chunk_mb[2] = {48, 48};
+  // apply kernels per precision: IWF_PATH_AUTO (pencil path where the geometry allows it),
+  // IWF_PATH_TILED or IWF_PATH_PENCIL
+  int path[2] = {IWF_PATH_AUTO, IWF_PATH_AUTO};
 };
 
 namespace iwf {
@@ -136,6 +140,11 @@ iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, cons
 iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, int* best,
                          cudaStream_t stream);
 iwf_status set_schedule_impl(iwf_plan* p, int precision, int threads, int tile_kb, int chunk_mb);
+iwf_status set_path_impl(iwf_plan* p, int precision, int path);
+// Reads (and clears) the apply error word after synchronising `stream`: IWF_ERR_TIMEOUT when
+// a pipelined apply kernel gave up waiting for one of its copies.
+iwf_status check_apply_error(iwf_plan* p, cudaStream_t stream);
+iwf_status get_schedule_impl(const iwf_plan* p, int precision, int* sched);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties

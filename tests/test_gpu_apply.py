@@ -167,9 +167,94 @@ def test_autotune_picks_a_valid_schedule(iwf):
     pb = W.config_moire(eps=0.5, K=8, L=8)
     plan = _plan(iwf, pb)
     ms, best = plan.autotune("c64", nvec=4)
-    assert ms > 0 and best[0] in (128, 256) and best[1] in (24, 48, 96, 160)
+    sched = plan.schedule("c64")
+    assert ms > 0 and best[2] in (12, 24, 48, 96) and sched["chunk_mb"] == best[2]
+    if sched["path"] == "pencil":
+        assert best[:2] == (0, 0)
+    else:
+        assert best[0] in (128, 256) and best[1] in (24, 48, 96, 160)
     win, Vg = _oracle(pb)
     X = W.random_block(win.N, 2, seed=1).astype(np.complex64).astype(np.complex128)
     got = _gpu_apply(plan, X, torch.complex64)
     want = O.apply_stencil(win, Vg, X)
     assert np.max(np.abs(got - want)) <= TOL32 * np.max(np.abs(want))
+
+
+# The pencil path: n = 4, d = 2, two equal k_I axis lengths and two equal k_II axis lengths,
+# each 16 or 32 (the moire family). Same tolerances as the tiled path.
+PENCIL = {
+    "moire16": W.config_moire(eps=0.5, K=8, L=8),
+    "moire16_phases": W.config_moire(eps=5.0, K=8, L=8, phases=[0.3, 1.1, 2.0, 4.0]),
+    "moire_kI16_kII32": W.config_moire(eps=0.5, K=8, L=16),
+    "moire_kI32_kII16": W.config_moire(eps=2.0, K=16, L=8, phases=[2.0, 0.1, 1.3, 5.9]),
+    # multi-axis modes: the potential is a full grid, not per-axis tables
+    "grid_pot": W.Problem("rnd4", W.random_P(2, 4, seed=7), (8, 8), (8, 8),
+                          *W.random_modes(4, 6, 3, seed=8)),
+}
+
+
+@pytest.mark.parametrize("name", list(PENCIL))
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_pencil_path_matches_oracle(iwf, name, prec):
+    pb = PENCIL[name]
+    plan = _plan(iwf, pb)
+    assert plan.schedule(prec)["path"] == "pencil"
+    win, Vg = _oracle(pb)
+    X = W.random_block(win.N, 3, seed=21)
+    if prec == "c64":
+        X = X.astype(np.complex64).astype(np.complex128)
+    got = _gpu_apply(plan, X, torch.complex128 if prec == "f64" else torch.complex64)
+    want = O.apply_stencil(win, Vg, X)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_pencil_and_tiled_paths_agree_full_size(iwf, prec):
+    # the benchmarked 16-vector block of the 32^4 grid through both kernel sets, with the
+    # oracle on two vectors; chunks of 2 vectors make the pencil path loop over chunks
+    pb = W.config_moire(eps=5.0)
+    plan = _plan(iwf, pb)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    X = W.random_block(plan.N, 16, seed=5)
+    if prec == "c64":
+        X = X.astype(np.complex64).astype(np.complex128)
+    plan.set_schedule(prec, 128, 96, 16 if prec == "c64" else 32)
+    got_p = _gpu_apply(plan, X, dtype)
+    plan.set_path(prec, "tiled")
+    got_t = _gpu_apply(plan, X, dtype)
+    tol = TOL64 if prec == "f64" else TOL32
+    scale = np.max(np.abs(got_t))
+    assert np.max(np.abs(got_p - got_t)) <= 2 * tol * scale
+    win, Vg = _oracle(pb)
+    for c in (0, 15):
+        want = O.apply_stencil(win, Vg, X[:, c])
+        assert np.max(np.abs(got_p[:, c] - want)) <= tol * np.max(np.abs(want))
+
+
+def test_path_selection(iwf):
+    from paper_2404_04507_gb300 import capi
+    plan = _plan(iwf, PROBS["moire_ragged"])
+    assert plan.schedule("f64")["path"] == "tiled"
+    with pytest.raises(capi.IwfError) as e:
+        plan.set_path("f64", "pencil")
+    assert e.value.status == -10
+    plan = _plan(iwf, PENCIL["moire16"])
+    plan.set_path("c64", "tiled")
+    assert plan.schedule("c64")["path"] == "tiled"
+    assert plan.schedule("f64")["path"] == "pencil"
+    plan.set_path("c64", "auto")
+    assert plan.schedule("c64")["path"] == "pencil"
+
+
+def test_overlapping_blocks_are_rejected(iwf):
+    from paper_2404_04507_gb300 import capi
+    pb = PENCIL["moire16"]
+    plan = _plan(iwf, pb)
+    x = torch.zeros((3, plan.N), dtype=torch.complex64, device="cuda")
+    with pytest.raises(capi.IwfError) as e:
+        plan.apply(x, x)
+    assert e.value.status == -1
+    with pytest.raises(capi.IwfError) as e:
+        plan.apply(x[:2], x[1:])                      # shifted by one vector
+    assert e.value.status == -1

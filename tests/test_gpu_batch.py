@@ -89,3 +89,26 @@ def test_batch_rejects_multi_axis_modes(iwf):
     with pytest.raises(capi.IwfError) as e:
         plan.batch_eigensolve([(m, c)], 4, block=4)
     assert e.value.status == -10
+
+
+@pytest.mark.parametrize("precision", ["f64", "c64"])
+def test_batch_on_pencil_path(iwf, precision):
+    # K = L = 8 (16^4 grid) runs the pencil kernels: per-problem potential tables and skipped
+    # converged problems inside them; the tiled kernels on the same batch give the same
+    # eigenvalues and the oracle certifies the residuals
+    params = [(0.7, [0.2, 1.4, 2.2, 0.9]), (5.0, [3.0, 0.3, 4.1, 1.7])]
+    probs, pots = _batch(8, params)
+    plan = iwf.Plan(probs[0].P, probs[0].K, probs[0].L)
+    assert plan.schedule(precision)["path"] == "pencil"
+    ev, X, res, iters, info = plan.batch_eigensolve(pots, 4, block=8, precision=precision,
+                                                    want_vectors=True)
+    assert info["converged"] == 1
+    plan.set_path("f64", "tiled")
+    plan.set_path("c64", "tiled")
+    ev_t, _, _, _, _ = plan.batch_eigensolve(pots, 4, block=8, precision=precision)
+    assert np.allclose(ev, ev_t, rtol=1e-10, atol=1e-10)
+    for q, pb in enumerate(probs):
+        win = O.build_window(pb.P, pb.K, pb.L)
+        Vg = O.grid_coefficients(pb.modes, pb.coef, win.lens)
+        Xq = X[q].cpu().numpy().T
+        assert np.max(O.eigen.residual_norms(win, Vg, Xq, ev[q])) <= 2e-10
