@@ -40,7 +40,7 @@ typedef enum {
 
 enum { IWF_METHOD_IWFPM = 0, IWF_METHOD_PM = 1 };
 enum { IWF_SHIFT_EXACT = 0, IWF_SHIFT_ROUND = 1 };
-enum { IWF_PREC_F64 = 0, IWF_PREC_C64 = 1 };
+enum { IWF_PREC_F64 = 0, IWF_PREC_C64 = 1, IWF_PREC_F64_EXACT = 2 };
 
 typedef struct iwf_plan iwf_plan; /* opaque, library-owned */
 
@@ -135,9 +135,14 @@ typedef struct {
   int maxit;        /* iteration limit over both phases (0: 1000)                            */
   double tol;       /* stop when |H~x_i - lambda_i x_i|_2 <= tol for i < nev, |x_i|_2 = 1
                        (0: 1e-10)                                                           */
-  int precision;    /* IWF_PREC_F64: every phase in complex double. IWF_PREC_C64: a first
-                       phase with complex-float blocks and apply (FP64 small problems) until
-                       the residuals reach c64_tol or stall, then complex double to tol    */
+  int precision;    /* IWF_PREC_F64: every phase in complex double; the tall-skinny Gram
+                       products and block updates run in double-float arithmetic on the FP32
+                       pipes (products exact by fma, sums by TwoSum: about 48 significant
+                       bits). IWF_PREC_F64_EXACT: the same with FP64 arithmetic in those
+                       contractions (slower on this GPU, whose FP64 rate is 1/62 of FP32).
+                       IWF_PREC_C64: a first phase with complex-float blocks and apply (FP64
+                       small problems) until the residuals reach c64_tol or stall, then the
+                       IWF_PREC_F64 phase to tol. Small problems are always FP64.          */
   double c64_tol;   /* residual target of the complex-float phase (0: 1e-4)                  */
   unsigned long long seed; /* seed of the start block when X0 is NULL                       */
 } iwf_solve_opts;

@@ -18,6 +18,14 @@ def _torch():
     return torch
 
 
+def _solve_precision(c, precision):
+    """Solver precision names: "f64", "c64" (complex-float first phase) or "f64_exact"."""
+    table = {"f64": c.IWF_PREC_F64, "c64": c.IWF_PREC_C64, "f64_exact": c.IWF_PREC_F64_EXACT}
+    if precision not in table:
+        raise ValueError(f"precision must be one of {sorted(table)}")
+    return table[precision]
+
+
 class Plan:
     """A window plan: P (d x n), K (d), L (n-d), method and shift mode (Sec. 3.1-3.2)."""
 
@@ -178,7 +186,7 @@ class Plan:
         torch = _torch()
         c = self._c
         opts = c.iwf_solve_opts(int(nev), int(block), int(maxit), float(tol),
-                                c.IWF_PREC_F64 if precision == "f64" else c.IWF_PREC_C64,
+                                _solve_precision(c, precision),
                                 float(c64_tol), int(seed))
         evals = np.zeros(nev)
         resid = np.zeros(nev)
@@ -212,7 +220,7 @@ class Plan:
                                for _, cf in potentials])
         re, im = np.ascontiguousarray(coef.real), np.ascontiguousarray(coef.imag)
         opts = c.iwf_solve_opts(int(nev), int(block), int(maxit), float(tol),
-                                c.IWF_PREC_F64 if precision == "f64" else c.IWF_PREC_C64,
+                                _solve_precision(c, precision),
                                 float(c64_tol), int(seed))
         evals = np.zeros((nprob, nev))
         resid = np.zeros((nprob, nev))

@@ -18,7 +18,7 @@ STATUS = {0: "IWF_OK", -1: "IWF_ERR_ARG", -2: "IWF_ERR_SINGULAR_PI", -3: "IWF_ER
           -10: "IWF_ERR_UNSUPPORTED"}
 IWF_METHOD_IWFPM, IWF_METHOD_PM = 0, 1
 IWF_SHIFT_EXACT, IWF_SHIFT_ROUND = 0, 1
-IWF_PREC_F64, IWF_PREC_C64 = 0, 1
+IWF_PREC_F64, IWF_PREC_C64, IWF_PREC_F64_EXACT = 0, 1, 2
 IWF_PATH_AUTO, IWF_PATH_TILED, IWF_PATH_PENCIL = 0, 1, 2
 
 

@@ -15,12 +15,47 @@ constexpr int kGramThreads = kGramTx * kGramTx;
 template <typename T> struct Acc { using type = double; };
 template <> struct Acc<float> { using type = float; };
 
+// ---- double-float arithmetic ------------------------------------------------------------
+// A double x is carried as an unevaluated sum hi + lo of two floats (hi = x rounded to float,
+// lo = the rest rounded to float: 48 significant bits). Products of two such pairs are formed
+// with the exact float product error from fma (Dekker); sums keep their rounding error with
+// TwoSum (Knuth). FP64 on this GPU runs at 1/62 of the FP32 rate, so a complex multiply-add in
+// this form (about 48 FP32 operations) costs about a fifth of its 4 FP64 fmas.
+struct DF4 { float rh, rl, ih, il; };              // complex: re (hi, lo), im (hi, lo)
+
+__device__ __forceinline__ DF4 df_split(double2 v) {
+  DF4 o;
+  o.rh = __double2float_rn(v.x);
+  o.rl = __double2float_rn(v.x - (double)o.rh);
+  o.ih = __double2float_rn(v.y);
+  o.il = __double2float_rn(v.y - (double)o.ih);
+  return o;
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (sh, sl) += (xh + xl)(yh + yl), dropping xl*yl (below 2^-48 relative)
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float t = fmaf(xh, yh, -p);                      // exact: xh*yh = p + t
+  t = fmaf(xh, yl, t);
+  t = fmaf(xl, yh, t);
+  float s, e;
+  two_sum(sh, p, s, e);
+  sh = s;
+  sl += e + t;
+}
+__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
+
 // G_partial[cta] = sum over this CTA's rows of conj(A_i,a) * B_i,c.
 // 24 x 24 threads; each owns a U x V micro-tile (outputs ty + 24u, tx + 24v), so the
 // launch picks U = ceil(ma/24), V = ceil(mb/24) and no thread multiplies padding.
 template <typename T, int U, int V>
 __global__ void __launch_bounds__(kGramThreads)
 gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
+  static_assert(U > 0 && V > 0, "tile");
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
   const int prob = blockIdx.y;
@@ -87,6 +122,72 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
     for (int v = 0; v < V; ++v) {
       const int a = ty + kGramTx * u, c = tx + kGramTx * v;
       if (a < ma && c < mb) out[a * mb + c] = make_double2(sumr[u][v], sumi[u][v]);
+    }
+}
+
+// Double-float variant of gram_kernel for complex-double blocks: the staged rows are split into
+// float pairs once, every product and sum runs on the FP32 pipes into one double-float
+// accumulator per output (TwoSum keeps each addition exact in the high part), and the CTA's
+// total is written as double.
+template <int U, int V>
+__global__ void __launch_bounds__(kGramThreads)
+gram_df_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const size_t poff = (size_t)prob * bt.pstride;
+  for (int i = 0; i < A.nb; ++i) A.p[i] = reinterpret_cast<const double2*>(A.p[i]) + poff;
+  for (int i = 0; i < B.nb; ++i) B.p[i] = reinterpret_cast<const double2*>(B.p[i]) + poff;
+  __shared__ DF4 sa[kGramRows][kMaxSmall + 1];
+  __shared__ DF4 sb[kGramRows][kMaxSmall + 1];
+  const int tx = threadIdx.x % kGramTx, ty = threadIdx.x / kGramTx;
+  float srh[U][V], srl[U][V], sih[U][V], sil[U][V];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < V; ++v) { srh[u][v] = srl[u][v] = sih[u][v] = sil[u][v] = 0.f; }
+  const long long ntiles = (N + kGramRows - 1) / kGramRows;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long r0 = t * kGramRows;
+    for (int e = threadIdx.x; e < kGramRows * ma; e += blockDim.x) {
+      const int k = e / kGramRows, r = e % kGramRows;
+      double2 v = make_double2(0.0, 0.0);
+      if (r0 + r < N) v = col_ptr<double>(A, k, N)[r0 + r];
+      sa[r][k] = df_split(v);
+    }
+    for (int e = threadIdx.x; e < kGramRows * mb; e += blockDim.x) {
+      const int k = e / kGramRows, r = e % kGramRows;
+      double2 v = make_double2(0.0, 0.0);
+      if (r0 + r < N) v = col_ptr<double>(B, k, N)[r0 + r];
+      sb[r][k] = df_split(v);
+    }
+    __syncthreads();
+    for (int r = 0; r < kGramRows; ++r) {
+      DF4 av[U], bv[V];
+#pragma unroll
+      for (int u = 0; u < U; ++u) av[u] = sa[r][min(ty + kGramTx * u, kMaxSmall)];
+#pragma unroll
+      for (int v = 0; v < V; ++v) bv[v] = sb[r][min(tx + kGramTx * v, kMaxSmall)];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          // conj(a) * b: re = ar br + ai bi, im = ar bi - ai br
+          df_mac(srh[u][v], srl[u][v], av[u].rh, av[u].rl, bv[v].rh, bv[v].rl);
+          df_mac(srh[u][v], srl[u][v], av[u].ih, av[u].il, bv[v].ih, bv[v].il);
+          df_mac(sih[u][v], sil[u][v], av[u].rh, av[u].rl, bv[v].ih, bv[v].il);
+          df_mac(sih[u][v], sil[u][v], -av[u].ih, -av[u].il, bv[v].rh, bv[v].rl);
+        }
+    }
+    __syncthreads();
+  }
+  double2* out = partial + ((size_t)prob * gridDim.x + blockIdx.x) * ma * mb;
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int a = ty + kGramTx * u, c = tx + kGramTx * v;
+      if (a < ma && c < mb)
+        out[a * mb + c] = make_double2(df_value(srh[u][v], srl[u][v]), df_value(sih[u][v], sil[u][v]));
     }
 }
 
@@ -171,6 +272,74 @@ update_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, cons
         V2 o; o.x = (T)a1r; o.y = (T)a1i;
         out1[gi] = o;
         if (C2) { V2 o2; o2.x = (T)a2r; o2.y = (T)a2i; out2[gi] = o2; }
+      }
+    }
+  }
+}
+
+// Double-float variant of update_kernel for complex-double blocks (same layout and
+// semantics; see gram_df_kernel for the arithmetic). One output element per thread is a sum of
+// at most 72 products, kept in one double-float accumulator.
+template <bool SUB>
+__global__ void __launch_bounds__(kUpdThreads)
+update_df_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, const double2* C2,
+                 int cstride, int q, double2* out1, double2* out2) {
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const size_t poff = (size_t)prob * bt.pstride;
+  for (int i = 0; i < S.nb; ++i) S.p[i] = reinterpret_cast<const double2*>(S.p[i]) + poff;
+  out1 += poff;
+  if (out2) out2 += poff;
+  C1 += (size_t)prob * cstride;
+  if (C2) C2 += (size_t)prob * cstride;
+  extern __shared__ __align__(16) unsigned char upd_raw[];
+  DF4* sc1 = reinterpret_cast<DF4*>(upd_raw);
+  DF4* sc2 = sc1 + kMaxSmall * kMaxBlock;
+  constexpr int rows = kUpdRows;
+  __shared__ DF4 ss[rows][kMaxSmall + 1];
+  for (int e = threadIdx.x; e < m * q; e += blockDim.x) {
+    sc1[e] = df_split(C1[e]);
+    if (C2) sc2[e] = df_split(C2[e]);
+  }
+  const int r = threadIdx.x / kMaxBlock, j = threadIdx.x % kMaxBlock;
+  const long long ntiles = (N + rows - 1) / rows;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long r0 = t * rows;
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+      const int k = e / rows, rr = e % rows;
+      double2 v = make_double2(0.0, 0.0);
+      if (r0 + rr < N) v = col_ptr<double>(S, k, N)[r0 + rr];
+      ss[rr][k] = df_split(v);
+    }
+    __syncthreads();
+    if (j < q && r0 + r < N) {
+      float a1rh = 0, a1rl = 0, a1ih = 0, a1il = 0, a2rh = 0, a2rl = 0, a2ih = 0, a2il = 0;
+      for (int k = 0; k < m; ++k) {
+        const DF4 sv = ss[r][k];
+        const DF4 c1 = sc1[k * q + j];
+        // s * c: re = sr cr - si ci, im = sr ci + si cr
+        df_mac(a1rh, a1rl, sv.rh, sv.rl, c1.rh, c1.rl);
+        df_mac(a1rh, a1rl, -sv.ih, -sv.il, c1.ih, c1.il);
+        df_mac(a1ih, a1il, sv.rh, sv.rl, c1.ih, c1.il);
+        df_mac(a1ih, a1il, sv.ih, sv.il, c1.rh, c1.rl);
+        if (C2) {
+          const DF4 c2 = sc2[k * q + j];
+          df_mac(a2rh, a2rl, sv.rh, sv.rl, c2.rh, c2.rl);
+          df_mac(a2rh, a2rl, -sv.ih, -sv.il, c2.ih, c2.il);
+          df_mac(a2ih, a2il, sv.rh, sv.rl, c2.ih, c2.il);
+          df_mac(a2ih, a2il, sv.ih, sv.il, c2.rh, c2.rl);
+        }
+      }
+      const size_t gi = (size_t)j * N + r0 + r;
+      if (SUB) {
+        double2 o = out1[gi];
+        o.x -= df_value(a1rh, a1rl);
+        o.y -= df_value(a1ih, a1il);
+        out1[gi] = o;
+      } else {
+        out1[gi] = make_double2(df_value(a1rh, a1rl), df_value(a1ih, a1il));
+        if (C2) out2[gi] = make_double2(df_value(a2rh, a2rl), df_value(a2ih, a2il));
       }
     }
   }
@@ -635,9 +804,13 @@ iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long lo
   if (g > slots_per_prob) g = slots_per_prob;
   const int U = (ma + kGramTx - 1) / kGramTx, V = (mb + kGramTx - 1) / kGramTx;
   const dim3 grid(g, bt.nprob);
+  const bool df = sizeof(T) == 8 && !bt.exact64;
   switch (U * 4 + V) {
 #define IWF_GRAM(U_, V_) \
-    case U_ * 4 + V_: gram_kernel<T, U_, V_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); break;
+    case U_ * 4 + V_: \
+      if (df) gram_df_kernel<U_, V_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); \
+      else gram_kernel<T, U_, V_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); \
+      break;
     IWF_GRAM(1, 1) IWF_GRAM(1, 2) IWF_GRAM(1, 3) IWF_GRAM(2, 1) IWF_GRAM(2, 2) IWF_GRAM(2, 3)
     IWF_GRAM(3, 1) IWF_GRAM(3, 2) IWF_GRAM(3, 3)
 #undef IWF_GRAM
@@ -674,6 +847,28 @@ iwf_status block_update(const Batch& bt, const BlockList& S, long long N, const 
       IWF_CUDA(cudaFuncSetAttribute(update_kernel<T, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     attr[subtract] = true;
+  }
+  if (sizeof(T) == 8 && !bt.exact64) {
+    static bool attr_df[2] = {false, false};
+    if (!attr_df[subtract]) {
+      if (subtract)
+        IWF_CUDA(cudaFuncSetAttribute(update_df_kernel<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      else
+        IWF_CUDA(cudaFuncSetAttribute(update_df_kernel<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      attr_df[subtract] = true;
+    }
+    if (subtract)
+      update_df_kernel<true><<<g, kUpdThreads, dyn, s>>>(bt, S, m, N, C1, nullptr, cstride, q,
+                                                         reinterpret_cast<double2*>(out1), nullptr);
+    else
+      update_df_kernel<false><<<g, kUpdThreads, dyn, s>>>(bt, S, m, N, C1, C2, cstride, q,
+                                                          reinterpret_cast<double2*>(out1),
+                                                          reinterpret_cast<double2*>(out2));
+    IWF_CUDA(cudaGetLastError());
+    count_launch();
+    return IWF_OK;
   }
   if (subtract)
     update_kernel<T, true><<<g, kUpdThreads, dyn, s>>>(bt, S, m, N, C1, nullptr, cstride, q,

@@ -43,6 +43,10 @@ struct Batch {
   int nprob;
   long long pstride;
   const int* active;
+  // complex-double blocks: 0 computes Gram products and block updates in double-float
+  // arithmetic on the FP32 pipes (products exact by fma, sums by TwoSum, about 48 bits),
+  // 1 in FP64 arithmetic
+  int exact64 = 0;
 };
 constexpr int kCapG = kMaxSmall * kMaxSmall;
 constexpr int kCapC = kMaxSmall * kMaxBlock;

@@ -125,7 +125,7 @@ struct Graph {
 template <typename T>
 iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxit, double tol,
                      int stall, void* Xio, Small& sm, Arena& ar, cudaStream_t st,
-                     PhaseResult& res) {
+                     PhaseResult& res, bool exact64) {
   using V2 = typename Cplx<T>::type;
   const int np = sm.nprob;
   const long long N = p->g.N;
@@ -137,7 +137,7 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
   IWF_TRY(ar.get(&HX2, all)); IWF_TRY(ar.get(&P2, all)); IWF_TRY(ar.get(&HP2, all));
   IWF_TRY(ar.get(&W2, all));
   X = reinterpret_cast<V2*>(Xio);
-  Batch bt{np, (long long)blk, sm.active};
+  Batch bt{np, (long long)blk, sm.active, exact64 ? 1 : 0};
   const int prec = prec_of<T>();
   std::vector<double> h_resid((size_t)np * kMaxBlock), h_theta((size_t)np * kMaxBlock);
   std::vector<int> h_status(np), h_active(np, 1);
@@ -335,14 +335,15 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
     if (X0) IWF_TRY((convert_block<double, float>(X0, Xf, 2 * (long long)all, st)));
     else IWF_TRY(random_block<float>(Xf, N, b * np, o->seed, st));
     const double tol1 = std::max(tol, o->c64_tol > 0 ? o->c64_tol : 1e-4);
-    IWF_TRY(run_phase<float>(p, ab, b, nev, maxit, tol1, 5, Xf, sm, ar, st, r1));
+    IWF_TRY(run_phase<float>(p, ab, b, nev, maxit, tol1, 5, Xf, sm, ar, st, r1, false));
     IWF_TRY((convert_block<float, double>(Xf, X, 2 * (long long)all, st)));
   } else {
     if (X0) IWF_CUDA(cudaMemcpyAsync(X, X0, sizeof(double2) * all, cudaMemcpyDeviceToDevice, st));
     else IWF_TRY(random_block<double>(X, N, b * np, o->seed, st));
   }
   const int left = std::max(1, maxit - r1.rounds);
-  IWF_TRY(run_phase<double>(p, ab, b, nev, left, tol, 0, X, sm, ar, st, r2));
+  IWF_TRY(run_phase<double>(p, ab, b, nev, left, tol, 0, X, sm, ar, st, r2,
+                            o->precision == IWF_PREC_F64_EXACT));
   if (evecs) {
     for (int q = 0; q < np; ++q)
       IWF_CUDA(cudaMemcpyAsync(reinterpret_cast<double2*>(evecs) + (size_t)q * N * nev,
@@ -381,7 +382,8 @@ iwf_status check_opts(const iwf_plan* p, const iwf_solve_opts* o) {
   if (nev < 1 || b < nev || b > kMaxBlock)
     return fail(IWF_ERR_ARG, "iwf_eigensolve: need 1 <= nev <= block <= 24");
   if ((long long)3 * b > p->g.N) return fail(IWF_ERR_ARG, "iwf_eigensolve: window too small for the block");
-  if (o->precision != IWF_PREC_F64 && o->precision != IWF_PREC_C64)
+  if (o->precision != IWF_PREC_F64 && o->precision != IWF_PREC_C64 &&
+      o->precision != IWF_PREC_F64_EXACT)
     return fail(IWF_ERR_ARG, "iwf_eigensolve: unknown precision");
   return IWF_OK;
 }

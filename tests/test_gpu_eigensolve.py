@@ -92,7 +92,7 @@ def _kronecker_surrogate(eps, K):
     return pb, O.eigen.kronecker_lowest(parts, 16)
 
 
-@pytest.mark.parametrize("precision", ["f64", "c64"])
+@pytest.mark.parametrize("precision", ["f64", "c64", "f64_exact"])
 def test_full_size_kronecker_surrogate(iwf, precision):
     # the 32^4 grid of the 2D moire workload, with P = [I2, diag(sqrt2, sqrt3)] and the
     # localised strength eps = 5 (the extended eps = 0.5 spectrum clusters its lowest 24
@@ -124,3 +124,30 @@ def test_eigensolve_argument_errors(iwf):
         plan.eigensolve(8, block=4)
     with pytest.raises(capi.IwfError):
         plan.eigensolve(25, block=25)
+
+
+@pytest.mark.parametrize("name", ["moire_ext", "pm_moire"])
+def test_double_float_contractions_match_fp64(iwf, name):
+    # "f64" runs the Gram products and block updates in double-float arithmetic on the FP32
+    # pipes, "f64_exact" in FP64: both must land on the dense oracle's eigenvalues and on each
+    # other to the solve tolerance, with residuals certified by the oracle's operator
+    pb = {"moire_ext": W.config_moire(eps=0.5, K=3, L=3),
+          "pm_moire": W.config_moire(eps=0.5, K=3, L=3, method="pm")}[name]
+    win = O.build_window(pb.P, pb.K, pb.L, method=pb.method)
+    Vg = O.grid_coefficients(pb.modes, pb.coef, win.lens)
+    ref = O.eigen.dense_eigs(win, Vg, 10)[0]
+    _, ev_df, X_df, _, info_df = _solve(iwf, pb, 10, 12, "f64")
+    _, ev_ex, _, _, info_ex = _solve(iwf, pb, 10, 12, "f64_exact")
+    assert info_df["converged"] == 1 and info_ex["converged"] == 1
+    assert _close(ev_df, ref) and _close(ev_ex, ref)
+    assert _close(ev_df, ev_ex)
+    r = O.eigen.residual_norms(win, Vg, X_df, ev_df)
+    assert np.max(r) <= 2e-10
+
+
+def test_unknown_solver_precision_is_rejected(iwf):
+    pb = W.config_1d()
+    plan = iwf.Plan(pb.P, pb.K, pb.L)
+    plan.set_potential(pb.modes, pb.coef)
+    with pytest.raises(ValueError):
+        plan.eigensolve(4, precision="f32")
