@@ -418,8 +418,8 @@ struct SmallShared {
   double w[kMaxSmall];
   double w2[kMaxSmall];
   double d[kMaxSmall];
-  double rc[kMaxSmall / 2 + 1], rs[kMaxSmall / 2 + 1];
-  double2 ph[kMaxSmall / 2 + 1];
+  float4 rot_cs[kMaxSmall / 2 + 1];   // Jacobi: c and s as float pairs (c.h, c.l, s.h, s.l)
+  float4 rot_ph[kMaxSmall / 2 + 1];   // Jacobi: e^{-i phi} as float pairs (re.h, re.l, im.h, im.l)
   int rp[kMaxSmall / 2 + 1], rq[kMaxSmall / 2 + 1];
   int idx[kMaxSmall];
   int perm[kMaxSmall];
@@ -444,8 +444,59 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+// ---- double-float scalars for the Jacobi rotations ---------------------------------------
+struct DF { float h, l; };
+__device__ __forceinline__ DF df_of(double x) {
+  DF o;
+  o.h = __double2float_rn(x);
+  o.l = __double2float_rn(x - (double)o.h);
+  return o;
+}
+__device__ __forceinline__ double df_dbl(DF a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ DF df_norm(float s, float e) {   // fast two-sum, |s| >= |e|
+  DF o;
+  o.h = s + e;
+  o.l = e - (o.h - s);
+  return o;
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e += a.l + b.l;
+  return df_norm(s, e);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
+// complex double-float, stored in the 16 bytes of a double2
+struct CDF { DF re, im; };
+__device__ __forceinline__ CDF cdf_mul(CDF a, CDF b) {
+  return CDF{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))),
+             df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+// c a - s t and s a + c t for real c, s
+__device__ __forceinline__ void cdf_rot(CDF a, CDF t, DF c, DF s, CDF& a2, CDF& t2) {
+  a2 = CDF{df_add(df_mul(c, a.re), df_neg(df_mul(s, t.re))),
+           df_add(df_mul(c, a.im), df_neg(df_mul(s, t.im)))};
+  t2 = CDF{df_add(df_mul(s, a.re), df_mul(c, t.re)), df_add(df_mul(s, a.im), df_mul(c, t.im))};
+}
+__device__ __forceinline__ CDF& cdf_at(double2* base, int e) {
+  return *reinterpret_cast<CDF*>(base + e);
+}
+__device__ __forceinline__ CDF cdf_of(double2 v) { return CDF{df_of(v.x), df_of(v.y)}; }
+__device__ __forceinline__ double2 dbl_of(CDF v) { return make_double2(df_dbl(v.re), df_dbl(v.im)); }
+
 // Eigen-decomposition of the Hermitian n x n matrix in sh.A (row-major, ld = n).
 // On return sh.w holds ascending eigenvalues and sh.V (row-major) the eigenvectors as columns.
+// The rotations run in double-float arithmetic on the FP32 pipes (A and V are held as float
+// pairs in place of their double2 entries while the sweeps run): this one-CTA solve sits on
+// the critical path of every iteration, and FP64 on this GPU issues at 1/62 of the FP32 rate.
+// Rotation angles are computed in FP64 from the double-float entries.
 __device__ void jacobi_eig(SmallShared& sh, int n) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < n * n; e += nt) {
@@ -467,20 +518,27 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
     __syncthreads();
     return;
   }
+  for (int e = tid; e < n * n; e += nt) {
+    cdf_at(sh.A, e) = cdf_of(sh.A[e]);
+    cdf_at(sh.V, e) = cdf_of(sh.V[e]);
+  }
+  __syncthreads();
   const int ne = n + (n & 1);       // players, with one dummy when n is odd
   const int np = ne / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    // convergence: off-diagonal Frobenius norm relative to the whole matrix
+    // convergence: off-diagonal Frobenius norm relative to the whole matrix, at the level
+    // double-float entries resolve (about 2^-46 each)
+    // (in double: the entries of a Gram of tiny columns would underflow when squared in float)
     double off = 0, tot = 0;
     for (int e = tid; e < n * n; e += nt) {
-      const double2 a = sh.A[e];
-      const double v = a.x * a.x + a.y * a.y;
+      const CDF a = cdf_at(sh.A, e);
+      const double v = (double)a.re.h * a.re.h + (double)a.im.h * a.im.h;
       tot += v;
       if (e / n != e % n) off += v;
     }
     off = block_sum(off, sh.red);
     tot = block_sum(tot, sh.red);
-    if (off <= 1e-30 * tot || off == 0.0) break;
+    if (off <= 1e-25 * tot || off == 0.0) break;
     if (tid == 0) sh.rot = 0;
     __syncthreads();
     for (int round = 0; round < ne - 1; ++round) {
@@ -489,14 +547,17 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
         const int posa = k, posb = ne - 1 - k;
         const int p = posa == 0 ? 0 : ((posa - 1 + round) % (ne - 1)) + 1;
         const int q = ((posb - 1 + round) % (ne - 1)) + 1;
+        // rotation annihilating a_pq, computed in FP64 from the double-float entries and
+        // stored as float pairs for the row and column updates
         double c = 1.0, s = 0.0;
         double2 eph = make_double2(1.0, 0.0);   // e^{-i phi}
         int pp = p < q ? p : q, qq = p < q ? q : p;
         if (qq < n) {
-          const double2 apq = sh.A[pp * n + qq];
+          const double2 apq = dbl_of(cdf_at(sh.A, pp * n + qq));
           const double r = hypot(apq.x, apq.y);
-          const double a = sh.A[pp * n + pp].x, bq = sh.A[qq * n + qq].x;
-          if (r > 1e-300 && r > 1e-18 * sqrt(fabs(a * bq))) {
+          const double a = df_dbl(cdf_at(sh.A, pp * n + pp).re);
+          const double bq = df_dbl(cdf_at(sh.A, qq * n + qq).re);
+          if (r > 1e-300 && r > 4e-14 * sqrt(fabs(a * bq))) {
             sh.rot = 1;
             eph = make_double2(apq.x / r, -apq.y / r);
             const double tau = (bq - a) / (2.0 * r);
@@ -507,28 +568,37 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
         } else {
           pp = -1;
         }
-        sh.rc[k] = c; sh.rs[k] = s; sh.ph[k] = eph; sh.rp[k] = pp; sh.rq[k] = qq;
+        sh.rp[k] = pp; sh.rq[k] = qq;
+        const DF cf = df_of(c), sf = df_of(s);
+        const CDF pf = cdf_of(eph);
+        sh.rot_cs[k] = make_float4(cf.h, cf.l, sf.h, sf.l);
+        sh.rot_ph[k] = make_float4(pf.re.h, pf.re.l, pf.im.h, pf.im.l);
       }
       __syncthreads();
       // columns: A <- A J, V <- V J
       for (int e = tid; e < n * np; e += nt) {
         const int i = e / np, k = e % np;
         const int p = sh.rp[k];
-        if (p < 0 || sh.rs[k] == 0.0) continue;
+        if (p < 0 || sh.rot_cs[k].z == 0.f) continue;
         const int q = sh.rq[k];
-        const double c = sh.rc[k], s = sh.rs[k];
-        const double2 eph = sh.ph[k];
+        const float4 cs = sh.rot_cs[k], ph = sh.rot_ph[k];
+        const DF c{cs.x, cs.y}, s{cs.z, cs.w};
+        const CDF eph{DF{ph.x, ph.y}, DF{ph.z, ph.w}};
         {
-          const double2 aip = sh.A[i * n + p], aiq = sh.A[i * n + q];
-          const double2 t = cmul(aiq, eph);
-          sh.A[i * n + p] = make_double2(c * aip.x - s * t.x, c * aip.y - s * t.y);
-          sh.A[i * n + q] = make_double2(s * aip.x + c * t.x, s * aip.y + c * t.y);
+          CDF& aip = cdf_at(sh.A, i * n + p);
+          CDF& aiq = cdf_at(sh.A, i * n + q);
+          const CDF t = cdf_mul(aiq, eph);
+          CDF a2, t2;
+          cdf_rot(aip, t, c, s, a2, t2);
+          aip = a2; aiq = t2;
         }
         {
-          const double2 vip = sh.V[i * n + p], viq = sh.V[i * n + q];
-          const double2 t = cmul(viq, eph);
-          sh.V[i * n + p] = make_double2(c * vip.x - s * t.x, c * vip.y - s * t.y);
-          sh.V[i * n + q] = make_double2(s * vip.x + c * t.x, s * vip.y + c * t.y);
+          CDF& vip = cdf_at(sh.V, i * n + p);
+          CDF& viq = cdf_at(sh.V, i * n + q);
+          const CDF t = cdf_mul(viq, eph);
+          CDF a2, t2;
+          cdf_rot(vip, t, c, s, a2, t2);
+          vip = a2; viq = t2;
         }
       }
       __syncthreads();
@@ -536,20 +606,29 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
       for (int e = tid; e < n * np; e += nt) {
         const int j = e / np, k = e % np;
         const int p = sh.rp[k];
-        if (p < 0 || sh.rs[k] == 0.0) continue;
+        if (p < 0 || sh.rot_cs[k].z == 0.f) continue;
         const int q = sh.rq[k];
-        const double c = sh.rc[k], s = sh.rs[k];
-        const double2 ephc = cconj(sh.ph[k]);   // e^{+i phi}
-        const double2 apj = sh.A[p * n + j], aqj = sh.A[q * n + j];
-        const double2 t = cmul(aqj, ephc);
-        sh.A[p * n + j] = make_double2(c * apj.x - s * t.x, c * apj.y - s * t.y);
-        sh.A[q * n + j] = make_double2(s * apj.x + c * t.x, s * apj.y + c * t.y);
+        const float4 cs = sh.rot_cs[k], ph = sh.rot_ph[k];
+        const DF c{cs.x, cs.y}, s{cs.z, cs.w};
+        const CDF ephc{DF{ph.x, ph.y}, DF{-ph.z, -ph.w}};   // e^{+i phi}
+        CDF& apj = cdf_at(sh.A, p * n + j);
+        CDF& aqj = cdf_at(sh.A, q * n + j);
+        const CDF t = cdf_mul(aqj, ephc);
+        CDF a2, t2;
+        cdf_rot(apj, t, c, s, a2, t2);
+        apj = a2; aqj = t2;
       }
       __syncthreads();
     }
     if (sh.rot == 0) break;
     __syncthreads();
   }
+  // back to double: eigenvalues on the diagonal, eigenvectors in V
+  for (int e = tid; e < n * n; e += nt) {
+    sh.A[e] = dbl_of(cdf_at(sh.A, e));
+    sh.V[e] = dbl_of(cdf_at(sh.V, e));
+  }
+  __syncthreads();
   // sort ascending: rank of every eigenvalue (ties by index)
   for (int i = tid; i < n; i += nt) sh.w2[i] = sh.A[i * n + i].x;
   __syncthreads();
