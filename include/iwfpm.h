@@ -143,7 +143,9 @@ typedef struct {
                        IWF_PREC_C64: a first phase with complex-float blocks and apply (FP64
                        small problems) until the residuals reach c64_tol or stall, then the
                        IWF_PREC_F64 phase to tol. Small problems are always FP64.          */
-  double c64_tol;   /* residual target of the complex-float phase (0: 1e-4)                  */
+  double c64_tol;   /* residual target of the complex-float phase (0: 1e-5); the phase also
+                       ends when its worst residual stops improving (a 30 % drop within
+                       10 iterations)                                                      */
   unsigned long long seed; /* seed of the start block when X0 is NULL                       */
 } iwf_solve_opts;
 

@@ -66,11 +66,14 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
   __shared__ V2 sa[kGramRows][kMaxSmall + 1];
   __shared__ V2 sb[kGramRows][kMaxSmall + 1];
   const int tx = threadIdx.x % kGramTx, ty = threadIdx.x / kGramTx;
-  double sumr[U][V], sumi[U][V];
+  // running sums across tiles: double for double blocks; for float blocks a float pair
+  // (hi, lo) kept with TwoSum, because adding into doubles would put one FP64 addition per
+  // output and tile on the slow FP64 pipe
+  AT sumr[U][V], sumi[U][V], lor[U][V], loi[U][V];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < V; ++v) { sumr[u][v] = 0; sumi[u][v] = 0; }
+    for (int v = 0; v < V; ++v) { sumr[u][v] = 0; sumi[u][v] = 0; lor[u][v] = 0; loi[u][v] = 0; }
   const long long ntiles = (N + kGramRows - 1) / kGramRows;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const long long r0 = t * kGramRows;
@@ -112,7 +115,15 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int v = 0; v < V; ++v) { sumr[u][v] += (double)accr[u][v]; sumi[u][v] += (double)acci[u][v]; }
+      for (int v = 0; v < V; ++v) {
+        if constexpr (sizeof(AT) == 4) {
+          float t, e;
+          two_sum(sumr[u][v], accr[u][v], t, e); sumr[u][v] = t; lor[u][v] += e;
+          two_sum(sumi[u][v], acci[u][v], t, e); sumi[u][v] = t; loi[u][v] += e;
+        } else {
+          sumr[u][v] += accr[u][v]; sumi[u][v] += acci[u][v];
+        }
+      }
     __syncthreads();
   }
   double2* out = partial + ((size_t)prob * gridDim.x + blockIdx.x) * ma * mb;
@@ -121,7 +132,9 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const int a = ty + kGramTx * u, c = tx + kGramTx * v;
-      if (a < ma && c < mb) out[a * mb + c] = make_double2(sumr[u][v], sumi[u][v]);
+      if (a < ma && c < mb)
+        out[a * mb + c] = make_double2((double)sumr[u][v] + (double)lor[u][v],
+                                       (double)sumi[u][v] + (double)loi[u][v]);
     }
 }
 
@@ -226,13 +239,15 @@ update_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, cons
   C1 += (size_t)prob * cstride;
   if (C2) C2 += (size_t)prob * cstride;
   extern __shared__ __align__(16) unsigned char upd_raw[];
-  double2* sc1 = reinterpret_cast<double2*>(upd_raw);
-  double2* sc2 = sc1 + kMaxSmall * kMaxBlock;
+  using C2T = typename Cplx<AT>::type;            // coefficients in the arithmetic type
+  C2T* sc1 = reinterpret_cast<C2T*>(upd_raw);
+  C2T* sc2 = sc1 + kMaxSmall * kMaxBlock;
   constexpr int rows = kUpdRows;                  // one thread per (row, j)
   __shared__ V2 ss[rows][kMaxSmall + 1];
   for (int e = threadIdx.x; e < m * q; e += blockDim.x) {
-    sc1[e] = C1[e];
-    if (C2) sc2[e] = C2[e];
+    C2T c; c.x = (AT)C1[e].x; c.y = (AT)C1[e].y;
+    sc1[e] = c;
+    if (C2) { C2T c2; c2.x = (AT)C2[e].x; c2.y = (AT)C2[e].y; sc2[e] = c2; }
   }
   const int r = threadIdx.x / kMaxBlock, j = threadIdx.x % kMaxBlock;  // r < kUpdRows
   const long long ntiles = (N + rows - 1) / rows;
@@ -250,13 +265,13 @@ update_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, cons
       AT a1r = 0, a1i = 0, a2r = 0, a2i = 0;
       for (int k = 0; k < m; ++k) {
         const V2 sv = ss[r][k];
-        const double2 c1 = sc1[k * q + j];
+        const C2T c1 = sc1[k * q + j];
         a1r = fma((AT)sv.x, (AT)c1.x, a1r);
         a1r = fma(-(AT)sv.y, (AT)c1.y, a1r);
         a1i = fma((AT)sv.x, (AT)c1.y, a1i);
         a1i = fma((AT)sv.y, (AT)c1.x, a1i);
         if (C2) {
-          const double2 c2 = sc2[k * q + j];
+          const C2T c2 = sc2[k * q + j];
           a2r = fma((AT)sv.x, (AT)c2.x, a2r);
           a2r = fma(-(AT)sv.y, (AT)c2.y, a2r);
           a2i = fma((AT)sv.x, (AT)c2.y, a2i);
