@@ -562,22 +562,31 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
         const int posa = k, posb = ne - 1 - k;
         const int p = posa == 0 ? 0 : ((posa - 1 + round) % (ne - 1)) + 1;
         const int q = ((posb - 1 + round) % (ne - 1)) + 1;
-        // rotation annihilating a_pq, computed in FP64 from the double-float entries and
-        // stored as float pairs for the row and column updates
+        // rotation annihilating a_pq, stored as float pairs for the row and column updates.
+        // The angle t = tan(theta) only needs to be close (a rotation by a slightly wrong
+        // angle leaves a tiny a_pq for the next sweep), so it is taken in FP32; c, s and the
+        // unit phase e^{-i phi} must be orthonormal to working precision and are formed in
+        // FP64 from that t. This keeps the chain of dependent FP64 operations per round
+        // short: it is the latency of every round of the small Jacobi solves.
         double c = 1.0, s = 0.0;
         double2 eph = make_double2(1.0, 0.0);   // e^{-i phi}
         int pp = p < q ? p : q, qq = p < q ? q : p;
         if (qq < n) {
           const double2 apq = dbl_of(cdf_at(sh.A, pp * n + qq));
-          const double r = hypot(apq.x, apq.y);
-          const double a = df_dbl(cdf_at(sh.A, pp * n + pp).re);
-          const double bq = df_dbl(cdf_at(sh.A, qq * n + qq).re);
-          if (r > 1e-300 && r > 4e-14 * sqrt(fabs(a * bq))) {
+          const double r2 = fma(apq.x, apq.x, apq.y * apq.y);
+          const DF ad = cdf_at(sh.A, pp * n + pp).re, bd = cdf_at(sh.A, qq * n + qq).re;
+          const double a = df_dbl(ad), bq = df_dbl(bd);
+          if (r2 > 1e-300 && r2 > 1.6e-27 * fabs(a * bq)) {
             sh.rot = 1;
-            eph = make_double2(apq.x / r, -apq.y / r);
-            const double tau = (bq - a) / (2.0 * r);
-            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+            const double inv_r = rsqrt(r2);
+            eph = make_double2(apq.x * inv_r, -apq.y * inv_r);
+            // tau = (a_qq - a_pp) / (2 |a_pq|) and t in FP32
+            const float tau = (float)((bq - a) * 0.5) * (float)inv_r;
+            const float at = fabsf(tau);
+            float tf = at > 1e15f ? 0.5f / at : 1.f / (at + sqrtf(fmaf(at, at, 1.f)));
+            if (tau < 0.f) tf = -tf;
+            const double t = (double)tf;
+            c = rsqrt(fma(t, t, 1.0));
             s = t * c;
           }
         } else {
