@@ -52,10 +52,12 @@ __device__ __forceinline__ double df_value(float h, float l) { return (double)h 
 // G_partial[cta] = sum over this CTA's rows of conj(A_i,a) * B_i,c.
 // 24 x 24 threads; each owns a U x V micro-tile (outputs ty + 24u, tx + 24v), so the
 // launch picks U = ceil(ma/24), V = ceil(mb/24) and no thread multiplies padding.
-template <typename T, int U, int V>
+// HERM (the product is Hermitian, ma == mb): only the 24 x 24 output blocks u <= v are
+// formed; reduce_partials mirrors the others.
+template <typename T, int U, int V, bool HERM>
 __global__ void __launch_bounds__(kGramThreads)
 gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
-  static_assert(U > 0 && V > 0, "tile");
+  static_assert(U > 0 && V > 0 && (!HERM || U == V), "tile");
   using V2 = typename Cplx<T>::type;
   using AT = typename Acc<T>::type;
   const int prob = blockIdx.y;
@@ -105,6 +107,7 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
+          if (HERM && u > v) continue;
           // conj(a) * b: re = ax bx + ay by, im = ax by - ay bx
           accr[u][v] = fma((AT)av[u].x, (AT)bv[v].x, accr[u][v]);
           accr[u][v] = fma((AT)av[u].y, (AT)bv[v].y, accr[u][v]);
@@ -116,6 +119,7 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int v = 0; v < V; ++v) {
+        if (HERM && u > v) continue;
         if constexpr (sizeof(AT) == 4) {
           float t, e;
           two_sum(sumr[u][v], accr[u][v], t, e); sumr[u][v] = t; lor[u][v] += e;
@@ -132,7 +136,7 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const int a = ty + kGramTx * u, c = tx + kGramTx * v;
-      if (a < ma && c < mb)
+      if (a < ma && c < mb && !(HERM && u > v))
         out[a * mb + c] = make_double2((double)sumr[u][v] + (double)lor[u][v],
                                        (double)sumi[u][v] + (double)loi[u][v]);
     }
@@ -142,9 +146,10 @@ gram_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, dou
 // float pairs once, every product and sum runs on the FP32 pipes into one double-float
 // accumulator per output (TwoSum keeps each addition exact in the high part), and the CTA's
 // total is written as double.
-template <int U, int V>
+template <int U, int V, bool HERM>
 __global__ void __launch_bounds__(kGramThreads)
 gram_df_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, double2* partial) {
+  static_assert(!HERM || U == V, "tile");
   const int prob = blockIdx.y;
   if (bt.active && !bt.active[prob]) return;
   const size_t poff = (size_t)prob * bt.pstride;
@@ -184,6 +189,7 @@ gram_df_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, 
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
+          if (HERM && u > v) continue;
           // conj(a) * b: re = ar br + ai bi, im = ar bi - ai br
           df_mac(srh[u][v], srl[u][v], av[u].rh, av[u].rl, bv[v].rh, bv[v].rl);
           df_mac(srh[u][v], srl[u][v], av[u].ih, av[u].il, bv[v].ih, bv[v].il);
@@ -199,25 +205,33 @@ gram_df_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N, 
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const int a = ty + kGramTx * u, c = tx + kGramTx * v;
-      if (a < ma && c < mb)
+      if (a < ma && c < mb && !(HERM && u > v))
         out[a * mb + c] = make_double2(df_value(srh[u][v], srl[u][v]), df_value(sih[u][v], sil[u][v]));
     }
 }
 
 // Sum the per-CTA partials in a fixed order (deterministic); problem blockIdx.y.
+// herm: entries in 24 x 24 blocks below the block diagonal were not formed; they are the
+// conjugates of their mirror images (mb = row length).
 __global__ void reduce_partials(Batch bt, const double2* partial, int slots, int count,
-                                double2* out) {
+                                double2* out, bool herm, int mb) {
   const int prob = blockIdx.y;
   if (bt.active && !bt.active[prob]) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= count) return;
+  int src = e;
+  bool conj = false;
+  if (herm) {
+    const int a = e / mb, c = e % mb;
+    if (a / kGramTx > c / kGramTx) { src = c * mb + a; conj = true; }
+  }
   const double2* pp = partial + (size_t)prob * slots * count;
   double re = 0, im = 0;
   for (int s = 0; s < slots; ++s) {
-    const double2 v = pp[(size_t)s * count + e];
+    const double2 v = pp[(size_t)s * count + src];
     re += v.x; im += v.y;
   }
-  out[(size_t)prob * kCapG + e] = make_double2(re, im);
+  out[(size_t)prob * kCapG + e] = make_double2(re, conj ? -im : im);
 }
 
 constexpr int kUpdRows = 16;
@@ -900,29 +914,32 @@ int grid_for(long long work, int per_block) {
 
 template <typename T>
 iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long long N, double2* out,
-                double2* partial, int slots_per_prob, cudaStream_t s) {
+                double2* partial, int slots_per_prob, cudaStream_t s, bool herm) {
   const int ma = A.nb * A.b, mb = B.nb * B.b;
   if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram: too many columns");
+  if (herm && ma != mb) return fail(IWF_ERR_ARG, "gram: a Hermitian product must be square");
   int g = grid_for(N, kGramRows);
   if (g > slots_per_prob) g = slots_per_prob;
   const int U = (ma + kGramTx - 1) / kGramTx, V = (mb + kGramTx - 1) / kGramTx;
   const dim3 grid(g, bt.nprob);
   const bool df = sizeof(T) == 8 && !bt.exact64;
-  switch (U * 4 + V) {
-#define IWF_GRAM(U_, V_) \
-    case U_ * 4 + V_: \
-      if (df) gram_df_kernel<U_, V_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); \
-      else gram_kernel<T, U_, V_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); \
+  switch (U * 4 + V + (herm ? 100 : 0)) {
+#define IWF_GRAM(U_, V_, H_) \
+    case U_ * 4 + V_ + (H_ ? 100 : 0): \
+      if (df) gram_df_kernel<U_, V_, H_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); \
+      else gram_kernel<T, U_, V_, H_><<<grid, kGramThreads, 0, s>>>(bt, A, B, ma, mb, N, partial); \
       break;
-    IWF_GRAM(1, 1) IWF_GRAM(1, 2) IWF_GRAM(1, 3) IWF_GRAM(2, 1) IWF_GRAM(2, 2) IWF_GRAM(2, 3)
-    IWF_GRAM(3, 1) IWF_GRAM(3, 2) IWF_GRAM(3, 3)
+    IWF_GRAM(1, 1, false) IWF_GRAM(1, 2, false) IWF_GRAM(1, 3, false) IWF_GRAM(2, 1, false)
+    IWF_GRAM(2, 2, false) IWF_GRAM(2, 3, false) IWF_GRAM(3, 1, false) IWF_GRAM(3, 2, false)
+    IWF_GRAM(3, 3, false) IWF_GRAM(1, 1, true) IWF_GRAM(2, 2, true) IWF_GRAM(3, 3, true)
 #undef IWF_GRAM
     default: return fail(IWF_ERR_ARG, "gram: shape");
   }
   IWF_CUDA(cudaGetLastError());
   count_launch();
   const int cnt = ma * mb;
-  reduce_partials<<<dim3((cnt + 255) / 256, bt.nprob), 256, 0, s>>>(bt, partial, g, cnt, out);
+  reduce_partials<<<dim3((cnt + 255) / 256, bt.nprob), 256, 0, s>>>(bt, partial, g, cnt, out,
+                                                                      herm, mb);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
@@ -1060,9 +1077,9 @@ iwf_status set_mask(const Batch& bt, int* mask, int off, int b, int value, const
 }
 
 template iwf_status gram<double>(const Batch&, const BlockList&, const BlockList&, long long,
-                                 double2*, double2*, int, cudaStream_t);
+                                 double2*, double2*, int, cudaStream_t, bool);
 template iwf_status gram<float>(const Batch&, const BlockList&, const BlockList&, long long,
-                                double2*, double2*, int, cudaStream_t);
+                                double2*, double2*, int, cudaStream_t, bool);
 template iwf_status block_update<double>(const Batch&, const BlockList&, long long, const double2*,
                                          const double2*, int, int, void*, void*, bool,
                                          cudaStream_t);

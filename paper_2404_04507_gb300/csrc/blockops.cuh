@@ -53,9 +53,11 @@ constexpr int kCapC = kMaxSmall * kMaxBlock;
 constexpr int kCapT = kMaxBlock * kMaxBlock;
 
 // Host-side launchers (defined in blockops.cu).
+// herm: the product is Hermitian (A^H A, or X^H H X for Hermitian H): only the blocks on and
+// above the 24 x 24 block diagonal are formed, the rest are mirrored.
 template <typename T>
 iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long long N, double2* out,
-                double2* partial, int slots_per_prob, cudaStream_t s);
+                double2* partial, int slots_per_prob, cudaStream_t s, bool herm = false);
 // out = S C1 (and out2 = S C2 when C2 != nullptr); subtract: out -= S C1 instead.
 // Problem p's coefficient matrices start at C1 + p*cstride (kCapG for Gram outputs,
 // kCapT for SVQB transforms, kCapC for Rayleigh-Ritz coefficients).

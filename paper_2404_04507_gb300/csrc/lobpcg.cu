@@ -159,7 +159,7 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
   };
   auto orthonormalize = [&](V2* Y, V2* Y2, int* mask) -> iwf_status {
     for (int pass = 0; pass < 2; ++pass) {
-      IWF_TRY(gram<T>(bt, blocks({Y}, b), blocks({Y}, b), N, sm.G, sm.partial, sm.slots, st));
+      IWF_TRY(gram<T>(bt, blocks({Y}, b), blocks({Y}, b), N, sm.G, sm.partial, sm.slots, st, true));
       IWF_TRY(svqb_small(bt, sm.G, b, 1e-14, sm.T, mask, sm.status, st));
       IWF_TRY(block_update<T>(bt, blocks({Y}, b), N, sm.T, nullptr, kCapT, b, Y2, nullptr, false, st));
       IWF_CUDA(cudaMemcpyAsync(Y, Y2, sizeof(V2) * all, cudaMemcpyDeviceToDevice, st));
@@ -168,7 +168,7 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
   };
   // Rayleigh-Ritz on X alone: X <- X Y, HX <- HX Y, theta (results land back in X, HX)
   auto rr_x = [&](V2* Xc, V2* HXc, V2* T1, V2* T2) -> iwf_status {
-    IWF_TRY(gram<T>(bt, blocks({Xc}, b), blocks({HXc}, b), N, sm.G, sm.partial, sm.slots, st));
+    IWF_TRY(gram<T>(bt, blocks({Xc}, b), blocks({HXc}, b), N, sm.G, sm.partial, sm.slots, st, true));
     IWF_TRY(set_mask(bt, sm.mask, 0, b, 1, nullptr, st));
     IWF_TRY(rayleigh_ritz_small(bt, sm.G, b, b, sm.mask, b, sm.theta, sm.Cx, sm.Cp, sm.maskp,
                                 sm.status, st));
@@ -191,7 +191,7 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
       IWF_TRY(block_update<T>(bt, XP, N, sm.G, nullptr, kCapG, b, W, nullptr, true, st));
     }
     for (int pass = 0; pass < 2; ++pass) {
-      IWF_TRY(gram<T>(bt, blocks({W}, b), blocks({W}, b), N, sm.G, sm.partial, sm.slots, st));
+      IWF_TRY(gram<T>(bt, blocks({W}, b), blocks({W}, b), N, sm.G, sm.partial, sm.slots, st, true));
       IWF_TRY(svqb_small(bt, sm.G, b, 1e-14, sm.T, sm.maskw, sm.status, st));
       IWF_TRY(block_update<T>(bt, blocks({W}, b), N, sm.T, nullptr, kCapT, b, W2, nullptr, false, st));
       std::swap(W, W2);
@@ -200,7 +200,8 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
     const int m = hasP ? 3 * b : 2 * b;
     const BlockList S = hasP ? blocks({Xa, W, Pa}, b) : blocks({Xa, W}, b);
     const BlockList HS = hasP ? blocks({HXa, HW, HPa}, b) : blocks({HXa, HW}, b);
-    IWF_TRY(gram<T>(bt, S, HS, N, sm.G, sm.partial, sm.slots, st));
+    // S^H H S is Hermitian (H is): only its upper 24 x 24 blocks are formed
+    IWF_TRY(gram<T>(bt, S, HS, N, sm.G, sm.partial, sm.slots, st, true));
     IWF_TRY(set_mask(bt, sm.mask, 0, b, 1, nullptr, st));
     IWF_TRY(set_mask(bt, sm.mask, b, b, 0, sm.maskw, st));
     if (hasP) IWF_TRY(set_mask(bt, sm.mask, 2 * b, b, 0, sm.maskp, st));
