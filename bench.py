@@ -64,7 +64,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,7 +80,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -198,6 +198,44 @@ def time_solves(iwf, torch, local, nev=16, block=24, eps=EPS, maxit=600, runs=No
                     "lambda_0": float(ev[0]), "lambda_last": float(ev[-1])}
         plan.close()
     return out
+
+
+def time_sweep(iwf, torch, local, count=8, KL=8, nev=16, block=24):
+    """Config-4 sweep subsample: the first `count` problems of the 256-problem distribution
+    (seed 4) whose cutoff maps to K = L = KL, solved to 1e-10 as one batched mixed-precision
+    solve and one by one; solves per second of each."""
+    eps, phases, cut, kl = W.sweep_params(256, seed=4)
+    idx = [i for i in range(256) if kl[i] == KL][:count]
+    probs = [W.sweep_problem(eps[i], phases[i], KL) for i in idx]
+    plan = iwf.Plan(probs[0].P, probs[0].K, probs[0].L, device=local)
+    pots = [(pb.modes, pb.coef) for pb in probs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    ev, _, res, iters, info = plan.batch_eigensolve(pots, nev, block=block, tol=1e-10,
+                                                    precision="c64", seed=7, raise_noconv=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    t_single, conv_single = 0.0, True
+    for pb in probs:
+        plan.set_potential(pb.modes, pb.coef)
+        e0.record()
+        _, _, _, inf1 = plan.eigensolve(nev, block=block, tol=1e-10, precision="c64", seed=7,
+                                        raise_noconv=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t_single += e0.elapsed_time(e1) / 1e3
+        conv_single = conv_single and bool(inf1["converged"])
+    plan.close()
+    return {"problems": len(probs), "grid": [2 * KL] * 4, "N": int((2 * KL) ** 4),
+            "precision": "mixed", "nev": nev, "block": block, "tol": 1e-10,
+            "batched": {"seconds": t_batch, "solves_per_s": len(probs) / t_batch,
+                        "iters": int(info["iters"]), "converged": bool(info["converged"]),
+                        "max_resid": float(np.max(res))},
+            "one_by_one": {"seconds": t_single, "solves_per_s": len(probs) / t_single,
+                           "converged": conv_single},
+            "sample": f"problems {idx} of W.sweep_params(256, seed=4) with K = L = {KL}"}
 
 
 def run_reference(args):
@@ -378,6 +416,7 @@ def run_ours(args):
            "d2h_bytes_per_step": nbytes}
 
     solve = None if args.no_solve else time_solves(iwf, torch, local)
+    sweep = None if (args.no_solve or args.no_sweep) else time_sweep(iwf, torch, local)
 
     if rank != 0:
         if ws > 1:
@@ -398,7 +437,7 @@ def run_ours(args):
                    "parallelism": f"replicas{ws}", "schedule": tune,
                    "l2": "inputs 268 MB > 129 MB L2; no flush needed"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "c64_apply": c64, "solve": solve,
+        "clocks": clk, "c64_apply": c64, "solve": solve, "sweep": sweep,
     }
     print(json.dumps(line))
     if ws > 1:
@@ -409,7 +448,7 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -417,6 +456,8 @@ def main(argv=None):
                     help="skip the time-to-eigenpairs measurement (IWFPM vs PM)")
     ap.add_argument("--fixed-schedule", action="store_true",
                     help="use the known tuned apply schedule instead of autotuning")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the config-4 sweep subsample (batched vs one-by-one solves)")
     ap.add_argument("--solve-only", action="store_true",
                     help="run one eigensolve and print its timing (profiling aid)")
     ap.add_argument("--solve-run", default="iwfpm_f64", choices=[r[0] for r in SOLVE_RUNS])
