@@ -151,3 +151,21 @@ def test_unknown_solver_precision_is_rejected(iwf):
     plan.set_potential(pb.modes, pb.coef)
     with pytest.raises(ValueError):
         plan.eigensolve(4, precision="f32")
+
+
+@pytest.mark.parametrize("precision", ["f64", "c64"])
+def test_qse3d_kronecker_spectrum(iwf, precision):
+    # the 3D QSE of the benchmark spec (P = [I3, sqrt2 I3], V = eps sum_j cos y_j + cos y_{j+3})
+    # at K = L = 4 (8^6 grid, three-axis groups): the window, Lambda and V all factor over the
+    # three spatial dimensions, so the exact spectrum is the Kronecker sum of three 1D problems
+    # P = [1, sqrt2]; nev = 4 takes the ground state and its threefold degenerate cluster
+    K = 4
+    pb = W.config_3d(eps=3.0, K=K, L=K)
+    m1, c1 = W.cosine_modes(2, 3.0)
+    w1 = O.build_window(np.array([[1.0, math.sqrt(2.0)]]), [K], [K])
+    e1 = O.eigen.dense_eigs(w1, O.grid_coefficients(m1, c1, w1.lens))[0]
+    ref = O.eigen.kronecker_lowest([e1, e1, e1], 4)
+    plan, ev, X, res, info = _solve(iwf, pb, 4, 12, precision)
+    assert plan.N == 8 ** 6
+    assert info["converged"] == 1 and np.max(res) <= 1e-10
+    assert _close(ev, ref), np.max(np.abs(ev - ref))
