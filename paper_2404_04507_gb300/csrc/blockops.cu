@@ -23,12 +23,33 @@ template <> struct Acc<float> { using type = float; };
 // this form (about 48 FP32 operations) costs about a fifth of its 4 FP64 fmas.
 struct DF4 { float rh, rl, ih, il; };              // complex: re (hi, lo), im (hi, lo)
 
+// x = hi + lo with integer and FP32 operations only: conversions between double and float,
+// and double arithmetic, issue on the slow FP64 pipe and made the staging of a tile cost as
+// much as its products. hi is x truncated to 24 significant bits (built from x's sign,
+// exponent and top fraction bits); lo is the remaining 29 fraction bits rounded to a float
+// (two exact 23-bit integer-to-float conversions by the 2^23 bias trick and one fma) times
+// the exact power of two 2^(e - 52). |x| < 2^-126 gives (0, 0); below 2^-75 lo is 0.
+__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const int e = (int)((hw >> 20) & 0x7ffu);          // biased exponent
+  const unsigned int sign = hw & 0x80000000u;
+  if (e < 1023 - 126) { hi = 0.f; lo = 0.f; return; }
+  const unsigned int top23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | top23);
+  const unsigned int rest = lw & 0x1fffffffu;
+  const float rh = __uint_as_float(0x4B000000u | (rest >> 23)) - 8388608.f;      // exact
+  const float rl = __uint_as_float(0x4B000000u | (rest & 0x7fffffu)) - 8388608.f;  // exact
+  const float r = fmaf(rh, 8388608.f, rl);
+  const int se = e - 1075 + 127;
+  const float scale = se > 0 ? __uint_as_float((unsigned int)se << 23) : 0.f;
+  lo = r * scale;
+  if (sign) lo = -lo;
+}
 __device__ __forceinline__ DF4 df_split(double2 v) {
   DF4 o;
-  o.rh = __double2float_rn(v.x);
-  o.rl = __double2float_rn(v.x - (double)o.rh);
-  o.ih = __double2float_rn(v.y);
-  o.il = __double2float_rn(v.y - (double)o.ih);
+  split_bits(v.x, o.rh, o.rl);
+  split_bits(v.y, o.ih, o.il);
   return o;
 }
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
