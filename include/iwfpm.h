@@ -260,6 +260,22 @@ iwf_status iwf_apply_profile(iwf_plan* plan, int precision, const void* psi, voi
                              int nvec, void* stream, double* pass_ms, int* launches);
 
 /*
+ * H~ psi (Sec. 4.1) for a block held in HOST memory.
+ *   psi_host, hpsi_host  host, N*nvec elements each, column-major, window order, complex
+ *                        double (IWF_PREC_F64) or complex float (IWF_PREC_C64); must not
+ *                        overlap. Page-locked memory gives the full copy bandwidth; pageable
+ *                        memory works, slower.
+ * The block crosses the device in chunks of vectors: the host-to-device copy of one chunk,
+ * the apply of the previous one and the device-to-host copy of the one before overlap on
+ * internal streams. Two input and two output chunk buffers are allocated by the plan on first
+ * use and kept until iwf_plan_destroy. The work is ordered after earlier work on `stream`
+ * (NULL: the legacy default stream) and the call returns when hpsi_host is complete. Same
+ * results as iwf_apply.
+ */
+iwf_status iwf_apply_host(iwf_plan* plan, int precision, const void* psi_host, void* hpsi_host,
+                          int nvec, void* stream);
+
+/*
  * Apply kernels. Both compute the same three passes (Sec. 4.1); they differ in how a pass
  * moves data:
  *   IWF_PATH_TILED   stages shared-memory tiles and runs every axis of a group on them; any

@@ -109,7 +109,7 @@ class Plan:
             return self._c.IWF_PREC_F64
         if t.dtype == torch.complex64:
             return self._c.IWF_PREC_C64
-        raise TypeError("vectors must be complex128 or complex64 CUDA tensors")
+        raise TypeError("vectors must be complex128 or complex64 tensors")
 
     def _check_block(self, t):
         torch = _torch()
@@ -119,6 +119,24 @@ class Plan:
         if t.numel() != nvec * self.N or not t.is_contiguous():
             raise ValueError("expected a contiguous (nvec, N) block in window order")
         return nvec
+
+    def apply_host(self, psi, out=None, stream=None):
+        """iwf_apply_host: H~ psi for a contiguous (nvec, N) or (N,) complex CPU tensor
+        (pinned memory gives the full copy bandwidth); returns when `out` is complete."""
+        torch = _torch()
+        if not isinstance(psi, torch.Tensor) or psi.is_cuda:
+            raise TypeError("expected a CPU tensor")
+        nvec = 1 if psi.dim() == 1 else psi.shape[0]
+        if psi.numel() != nvec * self.N or not psi.is_contiguous():
+            raise ValueError("expected a contiguous (nvec, N) block in window order")
+        if out is None:
+            out = torch.empty_like(psi, pin_memory=psi.is_pinned())
+        if out.is_cuda or out.dtype != psi.dtype or out.shape != psi.shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CPU tensor like psi")
+        self._c.check(self._c.iwf_apply_host(self.handle, self._prec(psi), C.c_void_p(psi.data_ptr()),
+                                             C.c_void_p(out.data_ptr()), int(nvec),
+                                             self._stream(stream)), "iwf_apply_host")
+        return out
 
     def apply(self, psi, out=None, stream=None):
         """H~ psi for a contiguous (nvec, N) or (N,) complex CUDA tensor (window order)."""

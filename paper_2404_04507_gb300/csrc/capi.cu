@@ -169,6 +169,7 @@ void iwf_plan_destroy(iwf_plan* p) {
   cudaFree(p->d_lam32);
   cudaFree(p->d_err);
   cudaFree(p->d_apply_err);
+  release_host_pipeline(p);
   cudaFree(p->d_tab64);
   cudaFree(p->d_tab32);
   cudaFree(p->d_grid64);
@@ -254,6 +255,14 @@ iwf_status iwf_plan_set_schedule(iwf_plan* p, int precision, int threads, int ti
                                  int chunk_mb) {
   if (!p) return fail(IWF_ERR_ARG, "iwf_plan_set_schedule: NULL plan");
   return set_schedule_impl(p, precision, threads, tile_kb, chunk_mb);
+}
+
+iwf_status iwf_apply_host(iwf_plan* p, int precision, const void* psi_host, void* hpsi_host,
+                          int nvec, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_apply_host: NULL plan");
+  DeviceGuard guard(p->device);
+  return apply_host_impl(p, precision, psi_host, hpsi_host, nvec, (cudaStream_t)stream);
 }
 
 iwf_status iwf_plan_set_path(iwf_plan* p, int precision, int path) {

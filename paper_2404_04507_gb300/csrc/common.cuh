@@ -113,6 +113,14 @@ struct iwf_plan {
   int tune_threads[2] = {256, 256};
   int tune_tile_kb[2] = {160, 160};
   int tune_chunk_mb[2] = {48, 48};
+  // host-block pipeline (iwf_apply_host): two input and two output chunk buffers, streams for
+  // host-to-device copies, compute and device-to-host copies, and the events that order them;
+  // created on first use
+  void* d_hin[2] = {nullptr, nullptr};
+  void* d_hout[2] = {nullptr, nullptr};
+  size_t host_chunk_bytes = 0;
+  cudaStream_t host_stream[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t host_ev[9] = {};
   // apply kernels per precision: IWF_PATH_AUTO (pencil path where the geometry allows it),
   // IWF_PATH_TILED or IWF_PATH_PENCIL
   int path[2] = {IWF_PATH_AUTO, IWF_PATH_AUTO};
@@ -131,6 +139,9 @@ iwf_status apply_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, i
                       const ApplyBatch* batch = nullptr);
 iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                               cudaStream_t stream);
+iwf_status apply_host_impl(iwf_plan* p, int precision, const void* psi_host, void* hpsi_host,
+                           int nvec, cudaStream_t stream);
+void release_host_pipeline(iwf_plan* p);
 iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
                            void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st);
 iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, const int* m,

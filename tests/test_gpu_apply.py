@@ -258,3 +258,37 @@ def test_overlapping_blocks_are_rejected(iwf):
     with pytest.raises(capi.IwfError) as e:
         plan.apply(x[:2], x[1:])                      # shifted by one vector
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_apply_host_matches_device_apply(iwf, prec, pinned):
+    # iwf_apply_host pipelines chunks of the block through the device; its result must equal
+    # iwf_apply's on the same vectors (same kernels), for 7 vectors in chunks of 2, 2, 2, 1
+    pb = PENCIL["moire16"]
+    plan = _plan(iwf, pb)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    X = W.random_block(plan.N, 7, seed=8)
+    xh = torch.from_numpy(np.ascontiguousarray(X.T)).to(dtype)
+    if pinned:
+        xh = xh.pin_memory()
+    yh = plan.apply_host(xh)
+    yd = plan.apply(xh.cuda()).cpu()
+    assert torch.equal(yh, yd)
+    win, Vg = _oracle(pb)
+    Xin = xh.numpy().T.astype(np.complex128)
+    want = O.apply_stencil(win, Vg, Xin[:, 6])
+    tol = TOL64 if prec == "f64" else TOL32
+    got = yh.numpy().T[:, 6].astype(np.complex128)
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+def test_apply_host_rejects_bad_arguments(iwf):
+    from paper_2404_04507_gb300 import capi
+    plan = _plan(iwf, PENCIL["moire16"])
+    x = torch.zeros((2, plan.N), dtype=torch.complex128)
+    with pytest.raises(capi.IwfError) as e:
+        plan.apply_host(x, x)
+    assert e.value.status == -1
+    with pytest.raises(TypeError):
+        plan.apply_host(x.cuda())
