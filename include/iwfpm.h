@@ -276,6 +276,17 @@ iwf_status iwf_apply_host(iwf_plan* plan, int precision, const void* psi_host, v
                           int nvec, void* stream);
 
 /*
+ * H~ psi by direct convolution instead of the FFT passes: Lambda psi + sum_m Vg_m psi(k* - m),
+ * the cyclic convolution on the K* grid with the potential's folded modes that F V F^{-1}
+ * equals (Sec. 3.3, Sec. 4.1, App. C). An ablation for potentials with few modes (at most
+ * 256 folded modes, else IWF_ERR_UNSUPPORTED; fastest k_I axis at most 32): its cost per
+ * point grows with the number of modes, the FFT passes' does not. Same arguments, layout and
+ * results (up to rounding) as iwf_apply; enqueues on `stream`.
+ */
+iwf_status iwf_apply_stencil(iwf_plan* plan, int precision, const void* psi, void* hpsi,
+                             int nvec, void* stream);
+
+/*
  * Apply kernels. Both compute the same three passes (Sec. 4.1); they differ in how a pass
  * moves data:
  *   IWF_PATH_TILED   stages shared-memory tiles and runs every axis of a group on them; any

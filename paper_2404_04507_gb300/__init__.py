@@ -120,6 +120,21 @@ class Plan:
             raise ValueError("expected a contiguous (nvec, N) block in window order")
         return nvec
 
+    def apply_stencil(self, psi, out=None, stream=None):
+        """iwf_apply_stencil: H~ psi by direct convolution with the folded modes (few-mode
+        potentials); same layout and result as apply()."""
+        nvec = self._check_block(psi)
+        if out is None:
+            out = _torch().empty_like(psi)
+        self._check_block(out)
+        if out.dtype != psi.dtype:
+            raise TypeError("psi and out must share a dtype")
+        self._c.check(self._c.iwf_apply_stencil(self.handle, self._prec(psi),
+                                                C.c_void_p(psi.data_ptr()),
+                                                C.c_void_p(out.data_ptr()), int(nvec),
+                                                self._stream(stream)), "iwf_apply_stencil")
+        return out
+
     def apply_host(self, psi, out=None, stream=None):
         """iwf_apply_host: H~ psi for a contiguous (nvec, N) or (N,) complex CPU tensor
         (pinned memory gives the full copy bandwidth); returns when `out` is complete."""

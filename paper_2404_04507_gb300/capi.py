@@ -70,6 +70,7 @@ _PROTOS = {
     "iwf_kernel_launches": (_ll, []),
     "iwf_apply_noalloc": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_apply_host": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
+    "iwf_apply_stencil": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_plan_autotune": (_i, [_vp, _i, _i, C.POINTER(C.c_double), C.POINTER(_i), _vp]),
     "iwf_plan_set_schedule": (_i, [_vp, _i, _i, _i, _i]),
     "iwf_plan_set_path": (_i, [_vp, _i, _i]),

@@ -169,6 +169,8 @@ void iwf_plan_destroy(iwf_plan* p) {
   cudaFree(p->d_lam32);
   cudaFree(p->d_err);
   cudaFree(p->d_apply_err);
+  cudaFree(p->d_stencil_m);
+  cudaFree(p->d_stencil_c);
   release_host_pipeline(p);
   cudaFree(p->d_tab64);
   cudaFree(p->d_tab32);
@@ -263,6 +265,14 @@ iwf_status iwf_apply_host(iwf_plan* p, int precision, const void* psi_host, void
   if (!p) return fail(IWF_ERR_ARG, "iwf_apply_host: NULL plan");
   DeviceGuard guard(p->device);
   return apply_host_impl(p, precision, psi_host, hpsi_host, nvec, (cudaStream_t)stream);
+}
+
+iwf_status iwf_apply_stencil(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                             void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_apply_stencil: NULL plan");
+  DeviceGuard guard(p->device);
+  return apply_stencil_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream);
 }
 
 iwf_status iwf_plan_set_path(iwf_plan* p, int precision, int path) {

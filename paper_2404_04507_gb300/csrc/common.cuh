@@ -106,6 +106,11 @@ struct iwf_plan {
   double voff_abs = 0.0;                  // sum_{m != 0} |Vg_m|
   double voff_sq = 0.0;                   // sum_{m != 0} |Vg_m|^2
   int tab_off[IWF_MAX_N] = {};
+  // folded modes of the potential for the direct-convolution apply (iwf_apply_stencil):
+  // stencil_m[q*n + j] in [0, lens[j]), coefficient stencil_c[q] = Vg (re, im)
+  int stencil_nm = 0;
+  int* d_stencil_m = nullptr;
+  double2* d_stencil_c = nullptr;
   // workspace for the apply
   void* d_work = nullptr;
   size_t work_bytes = 0;
@@ -141,6 +146,8 @@ iwf_status apply_noalloc_impl(iwf_plan* p, int precision, const void* psi, void*
                               cudaStream_t stream);
 iwf_status apply_host_impl(iwf_plan* p, int precision, const void* psi_host, void* hpsi_host,
                            int nvec, cudaStream_t stream);
+iwf_status apply_stencil_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
+                              cudaStream_t stream);
 void release_host_pipeline(iwf_plan* p);
 iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
                            void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st);

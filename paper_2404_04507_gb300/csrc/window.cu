@@ -349,6 +349,21 @@ iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* 
     IWF_CUDA(cudaGetLastError());
     p->pot_kind = 2;
   }
+  // the folded modes themselves, for the direct-convolution apply
+  cudaFree(p->d_stencil_m);
+  cudaFree(p->d_stencil_c);
+  p->d_stencil_m = nullptr;
+  p->d_stencil_c = nullptr;
+  p->stencil_nm = 0;
+  if (nm) {
+    std::vector<double2> coef(nm);
+    for (size_t q = 0; q < nm; ++q) coef[q] = make_double2(fre[q], fim[q]);
+    IWF_CUDA(cudaMalloc((void**)&p->d_stencil_m, nm * n * sizeof(int)));
+    IWF_CUDA(cudaMalloc((void**)&p->d_stencil_c, nm * sizeof(double2)));
+    IWF_CUDA(cudaMemcpy(p->d_stencil_m, fm.data(), nm * n * sizeof(int), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(p->d_stencil_c, coef.data(), nm * sizeof(double2), cudaMemcpyHostToDevice));
+  }
+  p->stencil_nm = (int)nm;
   IWF_CUDA(cudaDeviceSynchronize());
   return IWF_OK;
 }

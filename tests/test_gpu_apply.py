@@ -292,3 +292,33 @@ def test_apply_host_rejects_bad_arguments(iwf):
     assert e.value.status == -1
     with pytest.raises(TypeError):
         plan.apply_host(x.cuda())
+
+
+# Direct-convolution apply (the ablation of the FFT passes): same operator, every shape.
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_stencil_apply_matches_oracle(iwf, name, prec):
+    pb = PROBS[name]
+    plan = _plan(iwf, pb, pb.shift_round)
+    win, Vg = _oracle(pb, pb.shift_round)
+    X = W.random_block(win.N, 3, seed=31)
+    if prec == "c64":
+        X = X.astype(np.complex64).astype(np.complex128)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    xt = torch.from_numpy(np.ascontiguousarray(X.T)).to(dtype).cuda()
+    got = plan.apply_stencil(xt).cpu().numpy().astype(np.complex128).T
+    want = O.apply_stencil(win, Vg, X)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_stencil_and_fft_apply_agree_full_size(iwf, prec):
+    pb = W.config_moire(eps=5.0, phases=[0.4, 1.9, 3.3, 5.0])
+    plan = _plan(iwf, pb)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    x = torch.from_numpy(np.ascontiguousarray(W.random_block(plan.N, 4, seed=2).T)).to(dtype).cuda()
+    a = plan.apply(x)
+    b = plan.apply_stencil(x)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert float((a - b).abs().max()) <= 2 * tol * float(a.abs().max())
