@@ -472,12 +472,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 // unit k. The staged unit is read once into registers and its buffer then serves the
 // transpose; its lines are then dropped from L2 (the intermediate block is dead after this
 // pass). The unit's psi and Lambda are copied into a per-warp buffer as soon as the unit
-// starts, so that the copy overlaps the two DFTs, and H psi leaves with streaming stores. The
-// slice bounds lo of all slices sit in shared memory. Units of inactive batch problems are
+// starts, so that the copy overlaps the two DFTs, and H psi leaves with streaming stores. Each
+// unit's slice bounds are loaded before its wait. Units of inactive batch problems are
 // skipped.
 //
-// Shared memory: per warp STAGES staged units and psi and Lambda of one unit, then the lo
-// table (MII x 2 ints).
+// Shared memory: per warp STAGES staged units and psi and Lambda of one unit (56 KB per CTA
+// for complex float at L = 32: four CTAs per SM).
 template <typename T>
 __host__ __device__ constexpr size_t pipe_warp_bytes(int L, int stages) {
   return (size_t)stages * 32 * L * sizeof(typename Vec2<T>::type) +
@@ -499,8 +499,6 @@ __global__ void __launch_bounds__(WARPS * 32) pencil_c_pipe_kernel(PencilArgs a,
   V2* stages = reinterpret_cast<V2*>(wbase);
   V2* psi_s = stages + STAGES * UNIT;
   T* lam_s = reinterpret_cast<T*>(psi_s + UNIT);
-  int* lo_s = reinterpret_cast<int*>(smem_raw + (size_t)WARPS * WBYTES);
-  for (long long i = threadIdx.x; i < 2 * a.MII; i += blockDim.x) lo_s[i] = a.lo[i];
   if (lane == 0)
     for (int st = 0; st <= STAGES; ++st) mbar_init(smem_addr(&bars[warp][st]), 1);
   mbar_init_fence();
@@ -555,12 +553,13 @@ __global__ void __launch_bounds__(WARPS * 32) pencil_c_pipe_kernel(PencilArgs a,
                 LBYTES, bar);
     }
     psi_pending = true;
+    const long long o = (u % upv) * SPW + s;          // slice of this lane
+    const int lo0 = a.lo[2 * o], lo1 = a.lo[2 * o + 1];  // issued before the wait, which hides them
     const int st = k % STAGES;
     ok = mbar_wait(smem_addr(&bars[warp][st]), (uint32_t)((k / STAGES) & 1));
     if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
-    const long long o = (u % upv) * SPW + s;          // slice of this lane
     V2* U = stages + st * UNIT + s * LL;               // this lane's slice in the stage
-    const int off0 = roll_of(lo_s[2 * o], L), off1 = roll_of(lo_s[2 * o + 1], L);
+    const int off0 = roll_of(lo0, L), off1 = roll_of(lo1, L);
     T xr[L], xi[L];
     {
 #pragma unroll
@@ -834,7 +833,7 @@ iwf_status allow_smem(K* kernel, size_t bytes, size_t* allowed) {
 }
 
 // Pipelined pass C configuration: 2 warps per CTA, 2 stages per warp (56 KB with the psi and
-// Lambda buffers for complex float at L = 32, plus the lo table).
+// Lambda buffers for complex float at L = 32: four CTAs per SM).
 constexpr int kPipeWarps = 2, kPipeStages = 2;
 
 // Resident CTAs of `kernel` on the current device times its SM count, cached per device for
@@ -888,7 +887,7 @@ iwf_status launch_pencil_c_pipe(const PencilArgs& a, int nvec, int* err, cudaStr
                                 PassTimer* timer) {
   constexpr int W = kPipeWarps, SPW = 32 / L;
   const auto kernel = pencil_c_pipe_kernel<T, L, W, kPipeStages>;
-  const size_t smem = (size_t)W * pipe_warp_bytes<T>(L, kPipeStages) + 2 * a.MII * sizeof(int);
+  const size_t smem = (size_t)W * pipe_warp_bytes<T>(L, kPipeStages);
   static size_t allowed[64] = {};
   static OccCache occ;
   IWF_TRY(allow_smem(kernel, smem, allowed));
