@@ -59,3 +59,28 @@ def evaluate_quasi(win: Window, Ut: np.ndarray, x: np.ndarray) -> np.ndarray:
 def evaluate_parent(modes, coef, y: np.ndarray) -> np.ndarray:
     """U(y) = sum_m c_m e^{i m.y} at lifted points y (M, n)."""
     return np.exp(1j * (np.asarray(y) @ np.asarray(modes, dtype=np.float64).T)) @ np.asarray(coef)
+
+
+def normalise_field(u: np.ndarray):
+    """u0 / u0(xi*) with xi* the first point of largest modulus, and that index (Sec. 4.2: the
+    field is divided by its maximal modulus; the paper leaves the global phase free, and this
+    reading fixes it by making the field real and positive at xi*). |u|^2 is formed as
+    re*re + im*im with each step rounded, so that the choice of xi* is reproducible. A field
+    that is zero everywhere is returned unchanged with index 0."""
+    u = np.asarray(u, dtype=np.complex128)
+    a = u.real * u.real + u.imag * u.imag
+    i = int(np.argmax(a))
+    if a[i] == 0.0:
+        return u.copy(), 0
+    return u / u[i], i
+
+
+def density(u: np.ndarray) -> np.ndarray:
+    """rho = |u0|^2 of a normalised field (Sec. 4.2)."""
+    u = np.asarray(u, dtype=np.complex128)
+    return u.real * u.real + u.imag * u.imag
+
+
+def field_error(u: np.ndarray, u_ref: np.ndarray) -> float:
+    """E_f = ||u0 - u0*||_inf over the grid, both fields normalised (Sec. 4.2)."""
+    return float(np.max(np.abs(np.asarray(u) - np.asarray(u_ref)))) if len(u) else 0.0

@@ -149,6 +149,19 @@ def random_block(N: int, nvec: int, seed: int, dtype=np.complex128) -> np.ndarra
     return np.ascontiguousarray(x.astype(dtype)).T  # (N, nvec), each column contiguous
 
 
+def physical_grid(d: int, h: float = 0.1, half_width: float | None = None,
+                  rows: int | None = None) -> np.ndarray:
+    """Uniform grid on [-5a, 5a]^d, a = 10^(3-d), step h (the observation grid of Sec. 4.2:
+    10001 points in 1D, 1001^2 in 2D, 101^3 in 3D), as an (M, d) array, last axis fastest.
+    `rows` keeps only the first rows of the slowest axis (a bounded sample of the grid)."""
+    hw = 5.0 * 10.0 ** (3 - d) if half_width is None else half_width
+    cnt = int(round(2 * hw / h)) + 1
+    axis = -hw + h * np.arange(cnt)
+    axes = [axis[:rows] if (rows is not None and j == 0) else axis for j in range(d)]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.ascontiguousarray(np.stack([g.ravel() for g in mesh], axis=1))
+
+
 def random_P(d: int, n: int, seed: int) -> np.ndarray:
     """P = [I_d, Q0] with Q0 ~ U(-1.5, 1.5): generic irrational-looking entries."""
     rng = np.random.default_rng(seed)
