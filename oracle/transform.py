@@ -61,17 +61,21 @@ def evaluate_parent(modes, coef, y: np.ndarray) -> np.ndarray:
     return np.exp(1j * (np.asarray(y) @ np.asarray(modes, dtype=np.float64).T)) @ np.asarray(coef)
 
 
-def normalise_field(u: np.ndarray):
+def normalise_field(u: np.ndarray, at: int | None = None):
     """u0 / u0(xi*) with xi* the first point of largest modulus, and that index (Sec. 4.2: the
     field is divided by its maximal modulus; the paper leaves the global phase free, and this
     reading fixes it by making the field real and positive at xi*). |u|^2 is formed as
     re*re + im*im with each step rounded, so that the choice of xi* is reproducible. A field
-    that is zero everywhere is returned unchanged with index 0."""
+    that is zero everywhere is returned unchanged with index 0.
+
+    `at` gives xi* instead of searching for it. Comparing two fields needs one common point:
+    for an even potential H is real symmetric, u(-x) = conj(u(x)) and mirror points tie in
+    modulus exactly, so fields normalised at different twins differ by a phase factor."""
     u = np.asarray(u, dtype=np.complex128)
     a = u.real * u.real + u.imag * u.imag
-    i = int(np.argmax(a))
+    i = int(np.argmax(a)) if at is None else int(at)
     if a[i] == 0.0:
-        return u.copy(), 0
+        return u.copy(), (0 if at is None else i)
     return u / u[i], i
 
 

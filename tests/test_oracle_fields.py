@@ -22,6 +22,27 @@ def test_normalise_hand_example():
     assert np.array_equal(T.density(u), np.array([0.25, 1.0, 0.25]))
 
 
+def test_normalise_at_a_given_point():
+    u, i = T.normalise_field(np.array([1.0, -2.0, 1j]), at=2)
+    assert i == 2
+    assert np.array_equal(u, np.array([-1j, 2j, 1.0]))
+
+
+def test_mirror_twins_of_an_even_potential():
+    # V even and real: H~ is real symmetric in the k basis, so the ground state's coefficients
+    # are real up to one phase and u(-x) = conj(u(x)): |u| ties exactly at mirror points, and
+    # normalising at the two twins gives fields that differ by the phase factor u(x)/conj(u(x))
+    pb = W.config_1d(K=6, L=8, eps=3.0)
+    win = O.build_window(pb.P, pb.K, pb.L)
+    V = O.eigen.dense_eigs(win, O.grid_coefficients(pb.modes, pb.coef, win.lens), 1)[1][:, 0]
+    x = np.array([[-37.3], [37.3]])
+    u = T.evaluate_quasi(win, V, x)
+    assert abs(u[1] - np.conj(u[0])) <= 1e-13 * abs(u[0])
+    a, _ = T.normalise_field(u, at=0)
+    b, _ = T.normalise_field(u, at=1)
+    assert abs(T.field_error(a, b) - abs(u[0] / u[1] - 1) * abs(b[0])) <= 1e-13
+
+
 def test_normalise_ties_take_the_first_point():
     u, i = T.normalise_field(np.array([0.5, 2.0, -2.0, 2j]))
     assert i == 1
