@@ -40,6 +40,9 @@ EPS = 0.5
 # FP64 peak of a GB300 from its unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # = 1.26e12, i.e. the nominal 1.25 TFLOP/s. The FP64 passes are bound by it, not by HBM.
 FP64_PEAK_TFLOPS = 1.25
+# physical-space evaluation: rows of the 1001 x 1001 observation grid timed, repetitions
+EVAL_ROWS = 32
+EVAL_REPS = 3
 # pass-B kernel of the FP64 apply on the 32^4 grid, per kernel set
 PASS_B_KERNEL = {"pencil": "pencil_b_kernel<double,32,4>", "tiled": "pass_kernel<double,1>"}
 PROFILE_FILE = os.path.join(ROOT, "profiles", "pencil_pass_b_moire32_f64.txt")
@@ -425,6 +428,41 @@ def run_ours(args):
     stencil["note"] = (f"ablation, not the product path: direct convolution with the "
                        f"{nmodes_folded} folded modes; its cost grows with the number of modes")
 
+    # physical-space evaluation (iwf_evaluate) of one 32^4 coefficient vector on the 2D
+    # observation grid of the accuracy study ([-50, 50]^2, h = 0.1), a bounded sample of 32 of
+    # its 1001 rows, then normalisation and density (iwf_field_normalize)
+    evaluate = None
+    if not args.no_evaluate:
+        xg = torch.from_numpy(W.physical_grid(2, rows=EVAL_ROWS)).cuda()
+        coef = x[0].contiguous()
+        M = xg.shape[0]
+        u = plan.evaluate(coef, xg)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(EVAL_REPS):
+            plan.evaluate(coef, xg, out=u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ev = e0.elapsed_time(e1) / EVAL_REPS
+        e0.record(stream)
+        for _ in range(EVAL_REPS):
+            plan.normalize_field(u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_norm = e0.elapsed_time(e1) / EVAL_REPS
+        terms = float(M) * plan.N
+        tf_ev = 8.0 * terms / (ms_ev * 1e-3) / 1e12
+        evaluate = {
+            "value": terms / (ms_ev * 1e-3), "unit": "coefficient-point terms/s",
+            "ms": ms_ev, "points": M, "coefficients": plan.N,
+            "sample": f"{EVAL_ROWS} of 1001 rows of the [-50, 50]^2 grid, h = 0.1",
+            "full_grid_s": ms_ev * 1e-3 * 1001 / EVAL_ROWS,
+            "normalize_ms": ms_norm,
+            "roofline": {"bound": "alu", "achieved": tf_ev, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": tf_ev / FP64_PEAK_TFLOPS,
+                         "algorithmic_flops": "8 per coefficient and point (Horner: 4 FP64 "
+                                              "fmas)"}}
+
     # end to end through the C ABI with HOST buffers (iwf_apply_host: pinned host block in,
     # H psi back in host memory; the host-device copies of one chunk overlap the apply of
     # another inside the call)
@@ -466,7 +504,8 @@ def run_ours(args):
                    "parallelism": f"replicas{ws}", "schedule": tune,
                    "l2": "inputs 268 MB > 129 MB L2; no flush needed"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "c64_apply": c64, "stencil_ablation": stencil, "solve": solve,
+        "clocks": clk, "c64_apply": c64, "stencil_ablation": stencil, "evaluate": evaluate,
+        "solve": solve,
         "sweep": sweep,
     }
     print(json.dumps(line))
@@ -488,6 +527,8 @@ def main(argv=None):
                     help="use the known tuned apply schedule instead of autotuning")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the config-4 sweep subsample (batched vs one-by-one solves)")
+    ap.add_argument("--no-evaluate", action="store_true",
+                    help="skip the physical-space evaluation measurement")
     ap.add_argument("--solve-only", action="store_true",
                     help="run one eigensolve and print its timing (profiling aid)")
     ap.add_argument("--solve-run", default="iwfpm_f64", choices=[r[0] for r in SOLVE_RUNS])

@@ -276,6 +276,55 @@ iwf_status iwf_apply_host(iwf_plan* plan, int precision, const void* psi_host, v
                           int nvec, void* stream);
 
 /*
+ * Physical-space values u(x) = sum_{k in K_{K,L}} coef_k exp(i (P k).x) of the quasiperiodic
+ * function with window coefficients coef (Sec. 3.1, Eq. int), e.g. an eigenvector, at M
+ * points: the input of the paper's eigenfunction error E_f and density rho (Sec. 4.2).
+ *   coef  device, N complex double, window order
+ *   x     device, M x d doubles, row-major (point m at x + m*d)
+ *   u     device, M complex double (output)
+ * Direct summation in FP64, O(N M): each row along the fastest k_I axis by Horner's rule,
+ * row phases exact (sincos) whenever the second-fastest k_I axis wraps and advanced by one
+ * complex multiplication in between. Absolute errors are about (l_f + l_s + |theta|_max) eps
+ * sum|coef|, with l_f, l_s the two fastest k_I extents and theta = (P k).x.
+ * When M points fill too few CTAs, groups of slices are summed separately into a plan-owned
+ * scratch (at most 256 MiB, allocated on first need, freed by iwf_plan_destroy) and added in
+ * a fixed order: results do not depend on timing. Calls on one plan that overlap on the GPU
+ * share that scratch and race. Enqueues on `stream`; M = 0 is a no-op; M < 0 or a NULL
+ * pointer gives IWF_ERR_ARG.
+ */
+iwf_status iwf_evaluate(iwf_plan* plan, const void* coef, const double* x, long long M,
+                        void* u, void* stream);
+
+/*
+ * Normalises a physical-space field in place as the eigenfunction metrics of Sec. 4.2 do:
+ * u <- u / u(xi*), xi* the first point of largest |u|, so that max|u| = 1 and u is real and
+ * positive at xi* (the paper divides by the maximal modulus and leaves the phase free; fixing
+ * it there is this library's reading). |u|^2 is formed with each product and the sum rounded
+ * separately, so xi* is the same on any IEEE implementation; NaN points are never chosen; a
+ * field that is zero everywhere is left unchanged.
+ * To compare two fields (E_f), normalise both at one point: pass the reference's xi* as `at`.
+ * For an even real potential u(-x) = conj(u(x)), so mirror points tie in modulus exactly and
+ * fields normalised at different twins differ by a phase factor.
+ *   u       device, M complex double, in place
+ *   at      index of xi* to use, or -1 to search for the first point of largest |u|
+ *   rho     device, M doubles: the density |u|^2 after normalisation, or NULL
+ *   argmax  device, one long long: the index of xi* (-1 if no point qualified), or NULL
+ * Uses four words of plan-owned scratch: calls on one plan that overlap on the GPU race.
+ * Enqueues on `stream`; M = 0 is a no-op; M < 0, at >= M or u == NULL gives IWF_ERR_ARG.
+ */
+iwf_status iwf_field_normalize(iwf_plan* plan, void* u, long long M, long long at, double* rho,
+                               long long* argmax, void* stream);
+
+/*
+ * E_f = max_m |u_m - v_m| of two fields of M complex doubles (Sec. 4.2), written to `dist`
+ * (device, one double; 0 for M = 0, when u and v may be NULL). The square root is taken once,
+ * of the largest |u - v|^2. Same scratch and stream rules as iwf_field_normalize; M < 0 or a
+ * NULL dist gives IWF_ERR_ARG.
+ */
+iwf_status iwf_field_distance(iwf_plan* plan, const void* u, const void* v, long long M,
+                              double* dist, void* stream);
+
+/*
  * H~ psi by direct convolution instead of the FFT passes: Lambda psi + sum_m Vg_m psi(k* - m),
  * the cyclic convolution on the K* grid with the potential's folded modes that F V F^{-1}
  * equals (Sec. 3.3, Sec. 4.1, App. C). An ablation for potentials with few modes (at most

@@ -101,6 +101,8 @@ class Plan:
     def _stream(stream):
         if stream is None:
             return C.c_void_p(_torch().cuda.current_stream().cuda_stream)
+        if hasattr(stream, "cuda_stream"):          # torch.cuda.Stream
+            return C.c_void_p(stream.cuda_stream)
         return C.c_void_p(int(stream))
 
     def _prec(self, t):
@@ -119,6 +121,64 @@ class Plan:
         if t.numel() != nvec * self.N or not t.is_contiguous():
             raise ValueError("expected a contiguous (nvec, N) block in window order")
         return nvec
+
+    def evaluate(self, coef, x, out=None, stream=None):
+        """iwf_evaluate: u(x) = sum_k coef_k exp(i (P k).x) at the rows of x (M, d), for a
+        complex128 CUDA vector coef (N,) in window order; returns a complex128 CUDA (M,)."""
+        torch = _torch()
+        if not (isinstance(coef, torch.Tensor) and coef.is_cuda and coef.dtype == torch.complex128
+                and coef.numel() == self.N and coef.is_contiguous()):
+            raise TypeError("coef must be a contiguous complex128 CUDA vector of length N")
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64
+                and x.dim() == 2 and x.is_contiguous()):
+            raise TypeError("x must be a contiguous float64 CUDA tensor of shape (M, d)")
+        if x.shape[1] != self.d:
+            raise ValueError("x must have d = %d columns" % self.d)
+        M = x.shape[0]
+        if out is None:
+            out = torch.empty(M, dtype=torch.complex128, device=coef.device)
+        elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.complex128
+                  and out.numel() == M and out.is_contiguous()):
+            raise TypeError("out must be a contiguous complex128 CUDA vector of length M")
+        self._c.check(self._c.iwf_evaluate(self.handle, C.c_void_p(coef.data_ptr()),
+                                           C.c_void_p(x.data_ptr()), int(M),
+                                           C.c_void_p(out.data_ptr()), self._stream(stream)),
+                      "iwf_evaluate")
+        return out
+
+    @staticmethod
+    def _check_field(u, name):
+        torch = _torch()
+        if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.complex128
+                and u.dim() == 1 and u.is_contiguous()):
+            raise TypeError(name + " must be a contiguous complex128 CUDA vector")
+
+    def normalize_field(self, u, at=None, want_rho=True, stream=None):
+        """iwf_field_normalize: u <- u / u[i*] in place, i* = `at` if given, else the first
+        point of largest |u|; returns (rho = |u|^2 or None, i* as a CUDA int64 tensor)."""
+        torch = _torch()
+        self._check_field(u, "u")
+        M = u.shape[0]
+        rho = torch.empty(M, dtype=torch.float64, device=u.device) if want_rho else None
+        idx = torch.empty(1, dtype=torch.int64, device=u.device)
+        self._c.check(self._c.iwf_field_normalize(
+            self.handle, C.c_void_p(u.data_ptr()), int(M), -1 if at is None else int(at),
+            C.c_void_p(rho.data_ptr() if rho is not None else 0), C.c_void_p(idx.data_ptr()),
+            self._stream(stream)), "iwf_field_normalize")
+        return rho, idx
+
+    def field_distance(self, u, v, stream=None):
+        """iwf_field_distance: E_f = max |u - v| as a CUDA float64 tensor of one element."""
+        torch = _torch()
+        self._check_field(u, "u")
+        self._check_field(v, "v")
+        if u.shape != v.shape:
+            raise ValueError("u and v must have the same length")
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+        self._c.check(self._c.iwf_field_distance(
+            self.handle, C.c_void_p(u.data_ptr()), C.c_void_p(v.data_ptr()), int(u.shape[0]),
+            C.c_void_p(out.data_ptr()), self._stream(stream)), "iwf_field_distance")
+        return out
 
     def apply_stencil(self, psi, out=None, stream=None):
         """iwf_apply_stencil: H~ psi by direct convolution with the folded modes (few-mode

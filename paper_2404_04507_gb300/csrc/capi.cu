@@ -138,6 +138,8 @@ iwf_status plan_create(iwf_plan** out, int d, int n, const double* P, const int*
     st = fail(IWF_ERR_ALLOC, "cudaMalloc");
   if (st == IWF_OK && cudaMemset(p->d_apply_err, 0, sizeof(int)) != cudaSuccess)
     st = fail(IWF_ERR_CUDA, "cudaMemset");
+  if (st == IWF_OK && cudaMalloc((void**)&p->d_field, 4 * sizeof(unsigned long long)) != cudaSuccess)
+    st = fail(IWF_ERR_ALLOC, "cudaMalloc");
   if (st == IWF_OK) st = build_window_tables(p);
   if (st != IWF_OK) { iwf_plan_destroy(p); return st; }
   *out = p;
@@ -171,6 +173,8 @@ void iwf_plan_destroy(iwf_plan* p) {
   cudaFree(p->d_apply_err);
   cudaFree(p->d_stencil_m);
   cudaFree(p->d_stencil_c);
+  cudaFree(p->d_eval_part);
+  cudaFree(p->d_field);
   release_host_pipeline(p);
   cudaFree(p->d_tab64);
   cudaFree(p->d_tab32);
@@ -273,6 +277,30 @@ iwf_status iwf_apply_stencil(iwf_plan* p, int precision, const void* psi, void* 
   if (!p) return fail(IWF_ERR_ARG, "iwf_apply_stencil: NULL plan");
   DeviceGuard guard(p->device);
   return apply_stencil_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream);
+}
+
+iwf_status iwf_evaluate(iwf_plan* p, const void* coef, const double* x, long long M,
+                        void* u, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_evaluate: NULL plan");
+  DeviceGuard guard(p->device);
+  return evaluate_impl(p, coef, x, M, u, (cudaStream_t)stream);
+}
+
+iwf_status iwf_field_normalize(iwf_plan* p, void* u, long long M, long long at, double* rho,
+                               long long* argmax, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_field_normalize: NULL plan");
+  DeviceGuard guard(p->device);
+  return field_normalize_impl(p, u, M, at, rho, argmax, (cudaStream_t)stream);
+}
+
+iwf_status iwf_field_distance(iwf_plan* p, const void* u, const void* v, long long M,
+                              double* dist, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_field_distance: NULL plan");
+  DeviceGuard guard(p->device);
+  return field_distance_impl(p, u, v, M, dist, (cudaStream_t)stream);
 }
 
 iwf_status iwf_plan_set_path(iwf_plan* p, int precision, int path) {

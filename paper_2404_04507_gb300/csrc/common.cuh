@@ -111,6 +111,11 @@ struct iwf_plan {
   int stencil_nm = 0;
   int* d_stencil_m = nullptr;
   double2* d_stencil_c = nullptr;
+  // partial sums of iwf_evaluate's slice groups, grown on demand
+  double2* d_eval_part = nullptr;
+  size_t eval_part_bytes = 0;
+  // four words for the field reductions: max key, first index, multiplier (double2)
+  unsigned long long* d_field = nullptr;
   // workspace for the apply
   void* d_work = nullptr;
   size_t work_bytes = 0;
@@ -148,7 +153,13 @@ iwf_status apply_host_impl(iwf_plan* p, int precision, const void* psi_host, voi
                            int nvec, cudaStream_t stream);
 iwf_status apply_stencil_impl(iwf_plan* p, int precision, const void* psi, void* hpsi, int nvec,
                               cudaStream_t stream);
+iwf_status evaluate_impl(iwf_plan* p, const void* coef, const double* x, long long M,
+                         void* u, cudaStream_t stream);
 void release_host_pipeline(iwf_plan* p);
+iwf_status field_normalize_impl(iwf_plan* p, void* u, long long M, long long at, double* rho,
+                                long long* argmax, cudaStream_t stream);
+iwf_status field_distance_impl(iwf_plan* p, const void* u, const void* v, long long M,
+                               double* dist, cudaStream_t stream);
 iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0, double* evals,
                            void* evecs, double* resid, iwf_solve_info* info, cudaStream_t st);
 iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, const int* m,
