@@ -25,6 +25,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <vector>
+
 #include "common.cuh"
 #include "dft.cuh"
 
@@ -33,6 +35,7 @@ namespace iwf {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kLongThreads = 512;   // pass kernels of axis groups with a long axis
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
@@ -69,6 +72,7 @@ struct PassArgs {
   long long ld;             // element stride between vectors (= N)
   int tile_bytes;           // shared-memory bytes of the tile (pass B's V tables follow it)
   int vec_base;             // index of the launch's first vector in the whole block
+  const void* ltw[IWF_MAX_N];  // group axes longer than IWF_MAX_LEN: exp(2 pi i j / len)
 };
 
 // Roll offset of axis a for outer tile index o: pencil element k* lives at (k* + off) mod len.
@@ -134,6 +138,126 @@ __device__ void axis_dispatch(typename Vec2<T>::type* tile, const PassArgs& a, i
   }
 }
 
+// ---- axes longer than the codelets: in-place mixed-radix Stockham FFT in shared memory ----
+// A stage of radix R works on sub-transforms of size Ns (the product of the earlier radices).
+// Butterfly j of a pencil takes the elements j + r LEN/R (r < R), multiplies element r by
+// w^(r k LEN/(Ns R)) with k = j mod Ns and w = exp(S 2 pi i / LEN), combines them by an
+// R-point DFT and writes output r to (j / Ns) Ns R + k + r Ns. After the last stage the
+// pencil holds its DFT in natural order. Every thread first reads all its butterflies of a
+// stage into registers, the block synchronises, and then they are written, so the stages run
+// in place; the host keeps a tile at most long_stage_values(R) x blockDim elements. The roll
+// acts on the first stage's reads (gather) and on the last stage's writes (scatter), as in
+// axis_dft.
+__device__ __forceinline__ int pencil_base(const PassArgs& a, int gs, int len, int per_o, int p,
+                                           int* ot) {
+  const int o = p / per_o;
+  const int rem = p - o * per_o;
+  const int c = rem & ((1 << a.lc) - 1);
+  const int rest = rem >> a.lc;
+  const int q = rest / gs;
+  const int g0 = q * gs * len + (rest - q * gs);
+  *ot = o;
+  return ((o * a.M + g0) << a.lc) + c;
+}
+
+template <typename T, int R, int S, bool RL, bool RS>
+__device__ __forceinline__ void long_stage(typename Vec2<T>::type* tile, const PassArgs& a, int ax, int len,
+                           int Ns, bool first, bool last, const int* s_off) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int NB = 16 / R;                       // butterflies per thread and stage
+  const V2* __restrict__ tw = reinterpret_cast<const V2*>(a.ltw[ax]);
+  const int gs = a.grp.gs[ax];
+  const int step = gs << a.lc;
+  const int per_o = (a.M / len) << a.lc;
+  const int bpp = len / R;                         // butterflies per pencil
+  const int total = per_o * a.Ot * bpp;
+  const int tws = len / (Ns * R);
+  T vr[NB][R], vi[NB][R];
+#pragma unroll
+  for (int bb = 0; bb < NB; ++bb) {
+    const int b = threadIdx.x + bb * blockDim.x;
+    if (b < total) {
+      const int p = b / bpp, j = b - p * bpp;
+      int ot;
+      const int base = pencil_base(a, gs, len, per_o, p, &ot);
+      const int off = (RL && first) ? s_off[ot * IWF_MAX_N + ax] : 0;
+      const int k = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        int i = j + r * bpp;
+        if (RL && first) { i += off; if (i >= len) i -= len; }
+        const V2 v = tile[padx(base + i * step)];
+        T xr = v.x, xi = v.y;
+        const int e = r * k * tws;
+        if (e) {
+          const V2 w = __ldg(tw + e);
+          const T c = w.x, sn = S > 0 ? w.y : -w.y;
+          const T t = xr * c - xi * sn;
+          xi = xr * sn + xi * c;
+          xr = t;
+        }
+        vr[bb][r] = xr; vi[bb][r] = xi;
+      }
+      Butterfly<R, S, T>::run(vr[bb], vi[bb]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int bb = 0; bb < NB; ++bb) {
+    const int b = threadIdx.x + bb * blockDim.x;
+    if (b < total) {
+      const int p = b / bpp, j = b - p * bpp;
+      int ot;
+      const int base = pencil_base(a, gs, len, per_o, p, &ot);
+      const int off = (RS && last) ? s_off[ot * IWF_MAX_N + ax] : 0;
+      const int k = j % Ns;
+      const int o0 = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        int o = o0 + r * Ns;
+        if (RS && last) { o += off; if (o >= len) o -= len; }
+        V2 v; v.x = vr[bb][r]; v.y = vi[bb][r];
+        tile[padx(base + o * step)] = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int S, bool RL, bool RS>
+__device__ __forceinline__ void long_axis_fft(typename Vec2<T>::type* tile, const PassArgs& a, int ax,
+                              const int* s_off) {
+  const int len = a.grp.len[ax];
+  int Ns = 1;
+  for (int rem = len; rem > 1;) {
+    const int R = long_radix(rem);
+    const bool first = Ns == 1, last = rem == R;
+    switch (R) {
+#define IWF_STAGE(R_) case R_: long_stage<T, R_, S, RL, RS>(tile, a, ax, len, Ns, first, last, s_off); break;
+      IWF_STAGE(4) IWF_STAGE(2) IWF_STAGE(3) IWF_STAGE(5) IWF_STAGE(7)
+#undef IWF_STAGE
+      default: return;  // lengths are validated on the host
+    }
+    Ns *= R;
+    rem /= R;
+  }
+}
+
+// One axis of a group: register codelets, or in the LONG instantiation of the pass kernel
+// (groups with an axis longer than IWF_MAX_LEN) the shared-memory FFT for every axis of the
+// group, so that neither instantiation carries the other's register demand. Ends with the
+// block synchronised.
+template <typename T, int S, bool RL, bool RS, bool LONG>
+__device__ __forceinline__ void run_axis(typename Vec2<T>::type* tile, const PassArgs& a, int ax,
+                                         long long o0, const int* s_off) {
+  if constexpr (LONG) {
+    if (a.grp.len[ax] > 1) long_axis_fft<T, S, RL, RS>(tile, a, ax, s_off);
+  } else {
+    axis_dispatch<T, S, RL, RS>(tile, a, ax, o0, s_off);
+    __syncthreads();
+  }
+}
+
 template <typename T> __device__ __forceinline__ T pot_tab(const PotDev& p, long long off);
 template <> __device__ __forceinline__ double pot_tab<double>(const PotDev& p, long long off) { return p.tab64[off]; }
 template <> __device__ __forceinline__ float pot_tab<float>(const PotDev& p, long long off) { return p.tab32[off]; }
@@ -144,9 +268,10 @@ template <typename T> __device__ __forceinline__ T pot_const(const PotDev& p);
 template <> __device__ __forceinline__ double pot_const<double>(const PotDev& p) { return p.c64; }
 template <> __device__ __forceinline__ float pot_const<float>(const PotDev& p) { return p.c32; }
 
-// KIND 0: pass A, KIND 1: pass B, KIND 2: pass C.
-template <typename T, int KIND>
-__global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
+// KIND 0: pass A, KIND 1: pass B, KIND 2: pass C. LONG: the group has an axis longer than
+// IWF_MAX_LEN (run by pass_long_kernel).
+template <typename T, int KIND, bool LONG>
+__device__ __forceinline__ void pass_body(const PassArgs& a) {
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   V2* tile = reinterpret_cast<V2*>(smem_raw);
@@ -165,9 +290,11 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
   const V2* in = reinterpret_cast<const V2*>(a.in) + (size_t)vec * a.ld;
   V2* out = reinterpret_cast<V2*>(a.out) + (size_t)vec * a.ld;
 
-  for (int t = threadIdx.x; t < Ot * a.grp.ng; t += blockDim.x) {
+  // roll offsets of every outer slot of the tile; the slots past the last outer index of a
+  // partial tile get 0, so that the DFTs run on them (on unused data) stay inside the tile
+  for (int t = threadIdx.x; t < a.Ot * a.grp.ng; t += blockDim.x) {
     const int ot = t / a.grp.ng, ax = t % a.grp.ng;
-    s_off[ot * IWF_MAX_N + ax] = roll_off(a, ax, o0 + ot);
+    s_off[ot * IWF_MAX_N + ax] = ot < Ot ? roll_off(a, ax, o0 + ot) : 0;
   }
   // stage the tile: rows of C contiguous elements, one row per (outer, group point);
   // element e of the tile sits at (e >> lc) * inner + (e & (C-1)) from the tile's origin
@@ -197,15 +324,9 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
   __syncthreads();
 
   if (KIND == 0) {
-    for (int ax = 0; ax < a.grp.ng; ++ax) {
-      axis_dispatch<T, +1, true, false>(tile, a, ax, o0, s_off);
-      __syncthreads();
-    }
+    for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, +1, true, false, LONG>(tile, a, ax, o0, s_off);
   } else if (KIND == 1) {
-    for (int ax = 0; ax < a.grp.ng; ++ax) {
-      axis_dispatch<T, +1, true, false>(tile, a, ax, o0, s_off);
-      __syncthreads();
-    }
+    for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, +1, true, false, LONG>(tile, a, ax, o0, s_off);
     // multiply by V(y_l)/N: l_II from the group point, l_I from the inner index. With
     // per-axis tables V = [const + sum over k_I axes] + [sum over k_II axes]; both parts are
     // tabulated once per tile (vI over the C inner indices, vII over the M group points).
@@ -249,15 +370,9 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
       }
     }
     __syncthreads();
-    for (int ax = 0; ax < a.grp.ng; ++ax) {
-      axis_dispatch<T, -1, false, true>(tile, a, ax, o0, s_off);
-      __syncthreads();
-    }
+    for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, -1, false, true, LONG>(tile, a, ax, o0, s_off);
   } else {
-    for (int ax = 0; ax < a.grp.ng; ++ax) {
-      axis_dispatch<T, -1, false, true>(tile, a, ax, o0, s_off);
-      __syncthreads();
-    }
+    for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, -1, false, true, LONG>(tile, a, ax, o0, s_off);
   }
 
   V2* tout = out + org;
@@ -286,6 +401,16 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) {
     if (!done)
       for (int e = threadIdx.x; e < nel; e += blockDim.x) tout[gidx(e)] = tile[padx(e)];
   }
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads) pass_kernel(PassArgs a) { pass_body<T, KIND, false>(a); }
+
+// One CTA per SM is enough for these (a long axis fills the tile); the bound lets each thread
+// keep a whole FFT stage (16 complex values) in registers.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kLongThreads, 1) pass_long_kernel(PassArgs a) {
+  pass_body<T, KIND, true>(a);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -740,13 +865,29 @@ iwf_status init_twiddles(int device) {
   return IWF_OK;
 }
 
+// Values per thread the group's long axes allow for a stage (0: no axis above IWF_MAX_LEN).
+int long_group_values(const PassArgs& a) {
+  bool any = false;
+  for (int ax = 0; ax < a.grp.ng; ++ax) any = any || a.grp.len[ax] > IWF_MAX_LEN;
+  if (!any) return 0;
+  int v = 16;
+  for (int ax = 0; ax < a.grp.ng; ++ax) {
+    const int w = long_axis_values(a.grp.len[ax]);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
 // Choose C (inner chunk) and Ot (outer indices) for a group pass within tile_kb of smem.
 template <typename T>
 void choose_tile(PassArgs& a, int tile_kb) {
   // pass B (inner > 1) also keeps its group's V table (M values) next to the tile
   long long kb = (long long)tile_kb * 1024 - (a.inner > 1 ? (long long)a.M * sizeof(T) : 0);
   if (kb < 0) kb = 0;
-  const size_t budget = (size_t)kb / sizeof(typename Vec2<T>::type) * 32 / 33;
+  size_t budget = (size_t)kb / sizeof(typename Vec2<T>::type) * 32 / 33;
+  // a group with a long axis keeps every value of a shared-memory FFT stage in registers
+  const int vmin = long_group_values(a);
+  if (vmin > 0 && budget > (size_t)vmin * kLongThreads) budget = (size_t)vmin * kLongThreads;
   if (a.inner == 1) {
     a.C = 1;
     long long ot = (long long)(budget / a.M);
@@ -788,17 +929,24 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
   a.tile_bytes = (int)tbytes;
   const size_t bytes = tbytes + (KIND == 1 ? (size_t)(a.M + a.C) * sizeof(T) : 0);
   if (bytes > 200 * 1024) return fail(IWF_ERR_UNSUPPORTED, "apply: tile exceeds shared memory");
-  static bool attr_set[2][3] = {};
+  const int vmin = long_group_values(a);
+  if (vmin > 0) {
+    threads = kLongThreads;
+    if (elems > (size_t)vmin * kLongThreads)
+      return fail(IWF_ERR_UNSUPPORTED, "apply: axis group too large for the shared-memory FFT");
+  }
+  static bool attr_set[2][3][2] = {};
   const int ti = sizeof(T) == 8 ? 0 : 1;
-  if (!attr_set[ti][KIND]) {
-    IWF_CUDA(cudaFuncSetAttribute(pass_kernel<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    attr_set[ti][KIND] = true;
+  const int li = vmin > 0 ? 1 : 0;
+  auto kern = vmin > 0 ? pass_long_kernel<T, KIND> : pass_kernel<T, KIND>;
+  if (!attr_set[ti][KIND][li]) {
+    IWF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set[ti][KIND][li] = true;
   }
   const long long tiles = ((a.outer + a.Ot - 1) / a.Ot) * a.tiles_inner;
   dim3 grid((unsigned)tiles, (unsigned)nvec);
   if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
-  pass_kernel<T, KIND><<<grid, threads, bytes, stream>>>(a);
+  kern<<<grid, threads, bytes, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return timer ? stop_timer(timer, KIND, stream) : IWF_OK;
@@ -994,6 +1142,8 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     int s = 1;
     for (int j = d - 1; j >= 0; --j) { A.grp.gs[j] = s; s *= g.lens[j]; }
   }
+  for (int j = 0; j < d; ++j)
+    A.ltw[j] = sizeof(T) == 8 ? (const void*)p->d_ltw64[j] : (const void*)p->d_ltw32[j];
   choose_tile<T>(A, tile_kb);
 
   PassArgs B{};
@@ -1006,6 +1156,8 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     int s = 1;
     for (int j = n - d - 1; j >= 0; --j) { B.grp.gs[j] = s; s *= g.lens[d + j]; }
   }
+  for (int j = 0; j < n - d; ++j)
+    B.ltw[j] = sizeof(T) == 8 ? (const void*)p->d_ltw64[d + j] : (const void*)p->d_ltw32[d + j];
   choose_tile<T>(B, tile_kb);
 
   PassArgs Cp = A;
@@ -1139,6 +1291,37 @@ iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, 
     best[0] = bp == IWF_PATH_PENCIL ? 0 : bt;
     best[1] = bp == IWF_PATH_PENCIL ? 0 : bk;
     best[2] = bc;
+  }
+  return IWF_OK;
+}
+
+// exp(2 pi i j / len), j < len, in FP64 and FP32 (rounded from long double; the quarter
+// points are exact) for every axis of an axis group (k_I or k_II) that has an axis longer
+// than IWF_MAX_LEN: such groups run the shared-memory FFT on all their axes.
+iwf_status build_long_twiddles(iwf_plan* p) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  bool long_grp[2] = {false, false};
+  for (int j = 0; j < p->g.n; ++j)
+    if (p->g.lens[j] > IWF_MAX_LEN) long_grp[j < p->g.d ? 0 : 1] = true;
+  for (int j = 0; j < p->g.n; ++j) {
+    const int len = p->g.lens[j];
+    if (!long_grp[j < p->g.d ? 0 : 1]) continue;
+    std::vector<double2> h64(len);
+    std::vector<float2> h32(len);
+    for (int e = 0; e < len; ++e) {
+      long double c, sn;
+      if (e == 0) { c = 1; sn = 0; }
+      else if (2 * e == len) { c = -1; sn = 0; }
+      else if (4 * e == len) { c = 0; sn = 1; }
+      else if (4 * e == 3 * len) { c = 0; sn = -1; }
+      else { const long double t = two_pi * e / len; c = cosl(t); sn = sinl(t); }
+      h64[e] = make_double2((double)c, (double)sn);
+      h32[e] = make_float2((float)c, (float)sn);
+    }
+    IWF_CUDA(cudaMalloc(&p->d_ltw64[j], len * sizeof(double2)));
+    IWF_CUDA(cudaMalloc(&p->d_ltw32[j], len * sizeof(float2)));
+    IWF_CUDA(cudaMemcpy(p->d_ltw64[j], h64.data(), len * sizeof(double2), cudaMemcpyHostToDevice));
+    IWF_CUDA(cudaMemcpy(p->d_ltw32[j], h32.data(), len * sizeof(float2), cudaMemcpyHostToDevice));
   }
   return IWF_OK;
 }

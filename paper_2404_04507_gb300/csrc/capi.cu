@@ -110,8 +110,9 @@ iwf_status plan_create(iwf_plan** out, int d, int n, const double* P, const int*
   for (int j = 0; j < n; ++j) {
     const int h = j < d ? K[j] : L[j - d];
     if (h < 1) return fail(IWF_ERR_ARG, "iwf_plan_create: K and L must be >= 1");
-    if (2 * h > IWF_MAX_LEN)
-      return fail(IWF_ERR_UNSUPPORTED, "iwf_plan_create: axis length 2K or 2L above 32");
+    if (!axis_len_ok(2 * h))
+      return fail(IWF_ERR_UNSUPPORTED, "iwf_plan_create: axis length 2K or 2L above 8192, or "
+                                       "above 32 with a prime factor above 7");
     g.half[j] = h;
     g.lens[j] = 2 * h;
     g.N *= 2 * h;
@@ -141,6 +142,7 @@ iwf_status plan_create(iwf_plan** out, int d, int n, const double* P, const int*
   if (st == IWF_OK && cudaMalloc((void**)&p->d_field, 4 * sizeof(unsigned long long)) != cudaSuccess)
     st = fail(IWF_ERR_ALLOC, "cudaMalloc");
   if (st == IWF_OK) st = build_window_tables(p);
+  if (st == IWF_OK) st = build_long_twiddles(p);
   if (st != IWF_OK) { iwf_plan_destroy(p); return st; }
   *out = p;
   return IWF_OK;
@@ -175,6 +177,10 @@ void iwf_plan_destroy(iwf_plan* p) {
   cudaFree(p->d_stencil_c);
   cudaFree(p->d_eval_part);
   cudaFree(p->d_field);
+  for (int j = 0; j < IWF_MAX_N; ++j) {
+    cudaFree(p->d_ltw64[j]);
+    cudaFree(p->d_ltw32[j]);
+  }
   release_host_pipeline(p);
   cudaFree(p->d_tab64);
   cudaFree(p->d_tab32);

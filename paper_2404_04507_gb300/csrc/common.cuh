@@ -13,8 +13,42 @@
 #define IWF_MAX_N 8
 #define IWF_MAX_LEN 32       // largest axis length handled by the register DFT codelets
 #define IWF_MAX_GROUP 8192   // largest point count of one axis group staged in shared memory
+#define IWF_MAX_RADIX 7      // largest prime factor of an axis longer than IWF_MAX_LEN
 
 namespace iwf {
+
+// Radices of the shared-memory FFT of axes longer than IWF_MAX_LEN, in stage order: 4 while
+// it divides, then 2, 3, 5, 7.
+__host__ __device__ constexpr int long_radix(int n) {
+  return (n % 4 == 0) ? 4 : (n % 2 == 0) ? 2 : (n % 3 == 0) ? 3 : (n % 5 == 0) ? 5
+         : (n % 7 == 0) ? 7 : n;
+}
+
+// Values one thread holds for a stage of radix R: whole butterflies, at most 16 values.
+__host__ __device__ constexpr int long_stage_values(int R) { return R * (16 / R); }
+
+// true if an axis of this length is handled (short: codelets; long: prime factors <= 7)
+inline bool axis_len_ok(int len) {
+  if (len < 1 || len > IWF_MAX_GROUP) return false;
+  if (len <= IWF_MAX_LEN) return true;
+  for (int r = len; r > 1;) {
+    const int R = long_radix(r);
+    if (R > IWF_MAX_RADIX) return false;
+    r /= R;
+  }
+  return true;
+}
+
+// Smallest long_stage_values over the radices of an axis (16 for a power of two).
+inline int long_axis_values(int len) {
+  int v = 16;
+  for (int r = len; r > 1;) {
+    const int R = long_radix(r);
+    if (long_stage_values(R) < v) v = long_stage_values(R);
+    r /= R;
+  }
+  return v;
+}
 
 // Records a message for iwf_last_error() and returns the status unchanged.
 iwf_status fail(iwf_status st, const std::string& msg);
@@ -111,6 +145,10 @@ struct iwf_plan {
   int stencil_nm = 0;
   int* d_stencil_m = nullptr;
   double2* d_stencil_c = nullptr;
+  // exp(2 pi i j / len), j < len, for every axis of a group with an axis longer than
+  // IWF_MAX_LEN (null otherwise)
+  double2* d_ltw64[IWF_MAX_N] = {};
+  float2* d_ltw32[IWF_MAX_N] = {};
   // partial sums of iwf_evaluate's slice groups, grown on demand
   double2* d_eval_part = nullptr;
   size_t eval_part_bytes = 0;
@@ -156,6 +194,7 @@ iwf_status apply_stencil_impl(iwf_plan* p, int precision, const void* psi, void*
 iwf_status evaluate_impl(iwf_plan* p, const void* coef, const double* x, long long M,
                          void* u, cudaStream_t stream);
 void release_host_pipeline(iwf_plan* p);
+iwf_status build_long_twiddles(iwf_plan* p);
 iwf_status field_normalize_impl(iwf_plan* p, void* u, long long M, long long at, double* rho,
                                 long long* argmax, cudaStream_t stream);
 iwf_status field_distance_impl(iwf_plan* p, const void* u, const void* v, long long M,

@@ -322,3 +322,68 @@ def test_stencil_and_fft_apply_agree_full_size(iwf, prec):
     b = plan.apply_stencil(x)
     tol = TOL64 if prec == "f64" else TOL32
     assert float((a - b).abs().max()) <= 2 * tol * float(a.abs().max())
+
+
+# axes longer than the register codelets (32): the tiled passes run a shared-memory
+# mixed-radix FFT on every axis of such a group
+LONG = {
+    "qse1d_L20": W.config_1d(K=5, L=20),                              # 10 x 40 (4 2 5)
+    "ex41_L60": W.example_41(2.5, 5, 60),                             # 10 x 120 (4 2 3 5)
+    "pm_both_long": W.config_1d(K=24, L=64, method="pm"),             # 48 x 128
+    "moire_L20": W.config_moire(eps=0.5, K=3, L=20),                  # 6^2 x 40^2
+    "radix7_round": W.Problem("r7", np.array([[1.0, math.sqrt(7.0)]]), (21,), (3,),
+                              *W.cosine_modes(2, 1.5), shift_round=True),   # 42 (2 3 7) x 6
+}
+
+
+@pytest.mark.parametrize("name", list(LONG))
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_long_axes_match_oracle(iwf, name, prec):
+    pb = LONG[name]
+    plan = _plan(iwf, pb, pb.shift_round)
+    win, Vg = _oracle(pb, pb.shift_round)
+    assert np.array_equal(plan.window().astype(np.int64), win.k)
+    X = W.random_block(win.N, 3, seed=12)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    got = _gpu_apply(plan, X.astype(np.complex64) if prec == "c64" else X, dtype)
+    want = O.apply_stencil(win, Vg, X.astype(np.complex64).astype(np.complex128)
+                           if prec == "c64" else X)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_longest_axis_full_size(iwf, prec):
+    # 2L = 8192 (L = 4096, the paper's largest 1D window): one k_II group of 8192 points, the
+    # most a tile holds; 4 vectors, all checked
+    pb = W.config_1d(K=5, L=4096)
+    plan = _plan(iwf, pb)
+    win, Vg = _oracle(pb)
+    assert plan.N == 10 * 8192
+    X = W.random_block(win.N, 4, seed=13)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    got = _gpu_apply(plan, X.astype(np.complex64) if prec == "c64" else X, dtype)
+    want = O.apply_stencil(win, Vg, X.astype(np.complex64).astype(np.complex128)
+                           if prec == "c64" else X)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+def test_long_axis_limits(iwf):
+    from paper_2404_04507_gb300 import capi
+    for K in (17, 4097, 11 * 4):          # 34 = 2 x 17, 8194 > 8192, 88 = 8 x 11
+        with pytest.raises(capi.IwfError) as e:
+            iwf.Plan(np.array([[1.0, 2.0 ** 0.5]]), [K], [3])
+        assert e.value.status == -10
+
+
+@pytest.mark.parametrize("precision", ["f64", "c64"])
+def test_long_axis_eigensolve_matches_dense(iwf, precision):
+    # Example 4.1 at the paper's K = 5, L = 60 (10 x 120 grid): the solver on the long kernels
+    pb = W.example_41(2.5, 5, 60)
+    plan = _plan(iwf, pb)
+    win, Vg = _oracle(pb)
+    ev, X, res, info = plan.eigensolve(6, block=8, tol=1e-10, precision=precision)
+    ref = O.eigen.dense_eigs(win, Vg, 6)[0]
+    assert info["converged"] == 1
+    assert np.all(np.abs(ev - ref) <= 1e-10 * np.maximum(1.0, np.abs(ref))), np.max(np.abs(ev - ref))
