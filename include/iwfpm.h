@@ -66,8 +66,11 @@ const char* iwf_last_error(void);
  *          IWFPM: k_II in [-L,L)^{n-d}, k_I + Q k_II in [-K,K)^d with Q = P_I^{-1} P_II.
  *          PM: the box [-K,K)^d x [-L,L)^{n-d}.
  *   opts   host, may be NULL (IWFPM, exact shift, device 0).
- * Supported: every axis length 2K_j, 2L_j even in [2, 32]; (2K)^d and (2L)^{n-d} at most
- * 8192 each. The window, its slice bounds and Lambda = 1/2 |P k|^2 (Eq. discrete_Lambda)
+ * Supported: every axis length 2K_j, 2L_j in [2, 32], or in (32, 8192] with no prime factor
+ * above 7 (e.g. 40, 120, 1280, 8192); (2K)^d and (2L)^{n-d} at most 8192 each. Axis groups
+ * with an axis above 32 run a shared-memory FFT instead of the register codelets; a group
+ * holding more than 16 x 512 points per radix stage gives IWF_ERR_UNSUPPORTED at the apply.
+ * The window, its slice bounds and Lambda = 1/2 |P k|^2 (Eq. discrete_Lambda)
  * are built on the device; the call synchronises the device.
  * Errors: IWF_ERR_ARG, IWF_ERR_SINGULAR_PI, IWF_ERR_UNSUPPORTED, IWF_ERR_WINDOW_TIE,
  * IWF_ERR_ALLOC, IWF_ERR_CUDA. On error *plan is set to NULL.
@@ -339,7 +342,7 @@ iwf_status iwf_apply_stencil(iwf_plan* plan, int precision, const void* psi, voi
  * Apply kernels. Both compute the same three passes (Sec. 4.1); they differ in how a pass
  * moves data:
  *   IWF_PATH_TILED   stages shared-memory tiles and runs every axis of a group on them; any
- *                    geometry (axis lengths 2..32);
+ *                    geometry (every supported axis length);
  *   IWF_PATH_PENCIL  keeps one pencil per thread in registers, loaded from and stored to
  *                    global memory directly, with one shared-memory transpose per pass;
  *                    needs n = 4, d = 2 with 2K_1 = 2K_2 and 2L_1 = 2L_2, each 16 or 32;
