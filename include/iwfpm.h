@@ -170,9 +170,13 @@ typedef struct {
  *   X0     device, N*block complex doubles (window order, column-major) or NULL for a seeded
  *          random start (splitmix64 counter generator).
  *   evals  host, nev doubles, ascending.   resid host, nev doubles (may be NULL).
+ *          Each is the FP64 Rayleigh quotient x^H H~ x / x^H x of its returned vector, with
+ *          H~ x applied afresh after the iteration: O(resid^2 / gap) from the exact
+ *          eigenvalue, free of the Rayleigh-Ritz rounding (Ritz values differ by up to a few
+ *          1e-12 once the projected matrix has large entries).
  *   evecs  device, N*nev complex doubles, orthonormal, column-major, window order.
  *   info   host (may be NULL).
- * The call allocates its workspace (about 11 blocks of N*block complex values) and
+ * The call allocates its workspace (about 12 blocks of N*block complex values) and
  * synchronises `stream` before returning.
  * Errors: IWF_ERR_ARG, IWF_ERR_ALLOC, IWF_ERR_CUDA, IWF_ERR_NONFINITE, IWF_ERR_BREAKDOWN,
  * IWF_ERR_NOCONV (outputs then hold the last iterate).

@@ -1,0 +1,141 @@
+"""Accuracy studies of Sec. 4.2 on the GPU: E_v and E_f of ground states against a
+large-window reference solution, every step through the library's C ABI.
+
+For each window the ground state E_0, u_0 comes from iwf_eigensolve; u_0 is evaluated on
+the observation grid [-5a, 5a]^d, a = 10^(3-d), h = 0.1 (iwf_evaluate), normalised
+(iwf_field_normalize) and compared with the reference field (iwf_field_distance):
+  E_v = |E_0 - E_0*| / |E_0*|,   E_f = ||u_0 - u_0*||_inf.
+Both fields are normalised at the same point, the first point of largest |u_0*|: for the
+paper's even potentials u(-x) = conj(u(x)), so mirror points tie in modulus and fields
+normalised at different twins would differ by a phase factor.
+
+    python -m paper_2404_04507_gb300.accuracy --study ex41_v25
+prints one JSON line per window (DOF, iterations, solve seconds, E_v, E_f).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+
+from . import Plan
+from . import workloads as W
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def ground_state(pb, tol: float = 1e-10, precision: str = "f64", block: int = 16,
+                 maxit: int = 5000):
+    """Lowest eigenpair of one problem: dict with the plan, E0, the coefficient vector (a
+    complex128 CUDA tensor in window order), DOF, iterations, final residual, whether it met
+    `tol`, and solve seconds. The spectra of these problems cluster just above E0 (relative
+    gaps near 1e-4), so the block carries guard vectors (16 by default); a solve that stops
+    at `maxit` is reported with its residual, not raised."""
+    plan = Plan(pb.P, pb.K, pb.L, method=pb.method, shift_round=pb.shift_round)
+    plan.set_potential(pb.modes, pb.coef)
+    torch = _torch()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev, X, res, info = plan.eigensolve(1, block=block, tol=tol, maxit=maxit,
+                                       precision=precision, raise_noconv=False)
+    torch.cuda.synchronize()
+    return {"plan": plan, "E0": float(ev[0]), "coef": X[0].contiguous(), "dof": plan.N,
+            "iters": int(info["iters"]), "converged": int(info["converged"]),
+            "resid": float(res[0]), "seconds": time.perf_counter() - t0}
+
+
+def observe(gs, x, at=None):
+    """u_0 on the points x (a float64 CUDA tensor (M, d)), normalised in place at point `at`
+    (None: its own first point of largest modulus). Returns (u, index of that point)."""
+    u = gs["plan"].evaluate(gs["coef"], x)
+    _, idx = gs["plan"].normalize_field(u, at=at, want_rho=False)
+    return u, int(idx.item())
+
+
+def study(windows, reference, d: int, tol: float = 1e-10, precision: str = "f64",
+          grid_rows: int | None = None, maxit: int = 5000, fields: bool = True):
+    """E_v and E_f of every problem in `windows` against `reference` on the observation
+    grid of dimension d (the first `grid_rows` rows of it if given; fields=False skips E_f).
+    Yields one dict per window, the reference first."""
+    torch = _torch()
+    x = torch.from_numpy(W.physical_grid(d, rows=grid_rows)).cuda() if fields else None
+    ref = ground_state(reference, tol, precision, maxit=maxit)
+    u_ref, i_ref = observe(ref, x) if fields else (None, None)
+    yield {"name": reference.name, "method": reference.method, "K": list(reference.K),
+           "L": list(reference.L), "dof": ref["dof"], "E0": ref["E0"], "iters": ref["iters"],
+           "resid": ref["resid"], "converged": ref["converged"], "seconds": ref["seconds"],
+           "reference": True, "grid_points": int(x.shape[0]) if fields else 0}
+    for pb in windows:
+        gs = ground_state(pb, tol, precision, maxit=maxit)
+        ef = None
+        if fields:
+            u, _ = observe(gs, x, at=i_ref)
+            ef = float(gs["plan"].field_distance(u, u_ref).item())
+        yield {"name": pb.name, "method": pb.method, "K": list(pb.K), "L": list(pb.L),
+               "dof": gs["dof"], "E0": gs["E0"], "iters": gs["iters"], "resid": gs["resid"],
+               "seconds": gs["seconds"], "converged": gs["converged"],
+               "E_v": abs(gs["E0"] - ref["E0"]) / abs(ref["E0"]), "E_f": ef}
+
+
+# ---- the paper's studies (Sec. 4.2) ----
+
+def ex41_v25(Ls=(20, 40, 60), reference: str = "paper"):
+    """Example 4.1, v0 = 2.5: IWFPM K = 5 and PM K = 0.3L, 0.5L, 0.7L for L = 20, 40, 60,
+    against PM K = 640, L = 1024 (the table of E_v and E_f of Case 1). reference="iwfpm96"
+    takes IWFPM K = 5, L = 96 instead (seconds instead of minutes; by the same table the
+    L = 60 window is already within 3e-14 of the PM reference)."""
+    wins = []
+    for L in Ls:
+        wins.append(W.example_41(2.5, 5, L))
+        for f in (0.3, 0.5, 0.7):
+            wins.append(W.example_41(2.5, int(round(f * L)), L, method="pm"))
+    ref = (W.example_41(2.5, 640, 1024, method="pm") if reference == "paper"
+           else W.example_41(2.5, 5, 96))
+    return wins, ref, 1
+
+
+def ex41_v3(Ls=(256, 512, 1024, 2048)):
+    """Example 4.1, v0 = 3 (localised): IWFPM K = 8 on growing L against IWFPM K = 10,
+    L = 4096 (Case 2; the DOFs 4096 ... 32768 of its table are 16 L)."""
+    return [W.example_41(3.0, 8, L) for L in Ls], W.example_41(3.0, 10, 4096), 1
+
+
+def ex42(case: str = "I", Ls=(20, 30, 40, 50)):
+    """Example 4.2 case I (beta = 0.8 pi, theta = 0.2 pi), II (0.5 pi, 0.25 pi) or III
+    (0.5 pi, 0.2 pi): IWFPM K = 6 and PM K = 0.4L, 0.6L, 0.8L against IWFPM K = 10, L = 160."""
+    beta, theta = {"I": (0.8, 0.2), "II": (0.5, 0.25), "III": (0.5, 0.2)}[case]
+    beta, theta = beta * math.pi, theta * math.pi
+    wins = []
+    for L in Ls:
+        wins.append(W.example_42(beta, theta, 6, L))
+        for f in (0.4, 0.6, 0.8):
+            wins.append(W.example_42(beta, theta, int(round(f * L)), L, method="pm"))
+    return wins, W.example_42(beta, theta, 10, 160), 2
+
+
+STUDIES = {"ex41_v25": ex41_v25, "ex41_v25_fast": lambda: ex41_v25(reference="iwfpm96"),
+           "ex41_v3": ex41_v3, "ex42_I": lambda: ex42("I"),
+           "ex42_II": lambda: ex42("II"), "ex42_III": lambda: ex42("III")}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--study", choices=sorted(STUDIES), default="ex41_v25")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--maxit", type=int, default=5000)
+    ap.add_argument("--grid-rows", type=int, default=None,
+                    help="keep only the first rows of the observation grid (2D, 3D)")
+    args = ap.parse_args(argv)
+    wins, ref, d = STUDIES[args.study]()
+    for row in study(wins, ref, d, tol=args.tol, grid_rows=args.grid_rows, maxit=args.maxit):
+        print(json.dumps(row), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

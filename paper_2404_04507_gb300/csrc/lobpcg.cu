@@ -316,6 +316,88 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
   return IWF_OK;
 }
 
+// ---- returned eigenvalues: FP64 Rayleigh quotients of the returned vectors ----
+// theta_j = Re(x_j^H (H x)_j) / (x_j^H x_j) with H x applied afresh. The Ritz values of the
+// double-float Rayleigh-Ritz carry its rounding (a few 1e-12 when the projected matrix has
+// large entries); these quotients carry only FP64 rounding of two dot products and of one
+// apply, and differ from the exact eigenvalue by O(residual^2 / gap).
+constexpr int kRqThreads = 256;
+
+// vector v = q * nev + j (problem q, column j < nev) at offset (q * b + j) * N in X and Y;
+// block c of vector v writes its partial (num, den) to part[v * chunks + c]
+__global__ void __launch_bounds__(kRqThreads) rq_partial_kernel(
+    const double2* __restrict__ X, const double2* __restrict__ Y, long long N, int b, int nev,
+    int chunks, double2* __restrict__ part) {
+  const int v = blockIdx.y;
+  const int q = v / nev, j = v - q * nev;
+  const size_t off = ((size_t)q * b + j) * (size_t)N;
+  double num = 0.0, den = 0.0;
+  for (long long i = (long long)blockIdx.x * kRqThreads + threadIdx.x; i < N;
+       i += (long long)chunks * kRqThreads) {
+    const double2 x = X[off + i], y = Y[off + i];
+    num = fma(x.x, y.x, fma(x.y, y.y, num));
+    den = fma(x.x, x.x, fma(x.y, x.y, den));
+  }
+  for (int o = 16; o; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  __shared__ double sn[kRqThreads / 32], sd[kRqThreads / 32];
+  if ((threadIdx.x & 31) == 0) { sn[threadIdx.x >> 5] = num; sd[threadIdx.x >> 5] = den; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < kRqThreads / 32; ++w) { a += sn[w]; c += sd[w]; }
+    part[(size_t)v * chunks + blockIdx.x] = make_double2(a, c);
+  }
+}
+
+__global__ void rq_final_kernel(const double2* __restrict__ part, int chunks, int nvec,
+                                double* __restrict__ theta) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvec) return;
+  double a = 0.0, c = 0.0;
+  for (int k = 0; k < chunks; ++k) {
+    const double2 t = part[(size_t)v * chunks + k];
+    a += t.x;
+    c += t.y;
+  }
+  theta[v] = a / c;
+}
+
+// Rayleigh quotients of the first nev columns of every problem's block X (b columns each).
+iwf_status rayleigh_quotients(iwf_plan* p, const ApplyBatch* ab, Small& sm, Arena& ar,
+                              const double2* X, int b, int nev, double* out, long long* applies,
+                              cudaStream_t st) {
+  const int np = sm.nprob;
+  const long long N = p->g.N;
+  // one problem: apply only its nev columns; a batch: the whole block (its layout), with
+  // every problem switched on again
+  const int nvec = ab ? b * np : nev;
+  double2 *HX, *part;
+  double* d_theta;
+  IWF_TRY(ar.get(&HX, (size_t)N * nvec));
+  const int chunks = (int)std::min<long long>(512, (N + kRqThreads - 1) / kRqThreads);
+  IWF_TRY(ar.get(&part, (size_t)np * nev * chunks));
+  IWF_TRY(ar.get(&d_theta, (size_t)np * nev));
+  if (ab) {
+    const std::vector<int> ones(np, 1);
+    IWF_CUDA(cudaMemcpyAsync(sm.active, ones.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+  }
+  IWF_TRY(apply_impl(p, IWF_PREC_F64, X, HX, nvec, st, nullptr, ab));
+  *applies += nvec;
+  rq_partial_kernel<<<dim3((unsigned)chunks, (unsigned)(np * nev)), kRqThreads, 0, st>>>(
+      X, HX, N, ab ? b : nev, nev, chunks, part);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  rq_final_kernel<<<(np * nev + 127) / 128, 128, 0, st>>>(part, chunks, np * nev, d_theta);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  IWF_CUDA(cudaMemcpyAsync(out, d_theta, sizeof(double) * np * nev, cudaMemcpyDeviceToHost, st));
+  IWF_CUDA(cudaStreamSynchronize(st));
+  return IWF_OK;
+}
+
 // Shared driver: problems 0..np-1 with preconditioner parameters already on the device.
 iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opts* o,
                           Small& sm, Arena& ar, const void* X0, double* evals, void* evecs,
@@ -346,6 +428,9 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
   const int left = std::max(1, maxit - r1.rounds);
   IWF_TRY(run_phase<double>(p, ab, b, nev, left, tol, 0, X, sm, ar, st, r2,
                             o->precision == IWF_PREC_F64_EXACT));
+  std::vector<double> rq((size_t)np * nev);
+  long long rq_applies = 0;
+  IWF_TRY(rayleigh_quotients(p, ab, sm, ar, X, b, nev, rq.data(), &rq_applies, st));
   if (evecs) {
     for (int q = 0; q < np; ++q)
       IWF_CUDA(cudaMemcpyAsync(reinterpret_cast<double2*>(evecs) + (size_t)q * N * nev,
@@ -357,7 +442,7 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
   double worst = 0;
   for (int q = 0; q < np; ++q) {
     for (int j = 0; j < nev; ++j) {
-      evals[(size_t)q * nev + j] = r2.theta[(size_t)q * kMaxBlock + j];
+      evals[(size_t)q * nev + j] = rq[(size_t)q * nev + j];
       const double r = r2.resid[(size_t)q * kMaxBlock + j];
       if (resid) resid[(size_t)q * nev + j] = r;
       worst = std::max(worst, r);
@@ -368,7 +453,7 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
   if (info) {
     info->iters = r1.rounds + r2.rounds;
     info->iters_c64 = r1.rounds;
-    info->applies = r1.applies + r2.applies;
+    info->applies = r1.applies + r2.applies + rq_applies;
     info->converged = all_conv ? 1 : 0;
     info->max_resid = worst;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

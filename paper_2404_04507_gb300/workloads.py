@@ -123,6 +123,32 @@ def example_41(v0: float = 2.5, K: int = 5, L: int = 60, method: str = "iwfpm",
                    meta={"v0": v0})
 
 
+def example_42(beta: float, theta: float, K: int = 6, L: int = 20, method: str = "iwfpm",
+               shift_round: bool = False) -> Problem:
+    """Example 4.2: v = 4 - [cos b x1 + 2 cos b x2 + cos(b x1 cos t + b x2 sin t)],
+    P = b [[1, 0, cos t], [0, 1, sin t]], V(y) = 4 - (cos y1 + 2 cos y2 + cos y3)."""
+    c, s = math.cos(theta), math.sin(theta)
+    if abs(theta - math.pi / 4) < 1e-15:
+        c = s = math.sqrt(0.5)
+    P = beta * np.array([[1.0, 0.0, c], [0.0, 1.0, s]])
+    m, co = cosine_modes(3, [-1.0, -2.0, -1.0], const=4.0)
+    return Problem("ex42", P, (K, K), (L,), m, co, method=method, shift_round=shift_round,
+                   meta={"beta": beta, "theta": theta})
+
+
+def example_43(beta: float, K: int = 5, L: int = 10, theta: float = 0.2 * math.pi,
+               method: str = "iwfpm", shift_round: bool = False) -> Problem:
+    """Example 4.3: v = 6 - [cos b x1 + cos b x2 + cos b x3 + cos(b x1 cos t + b x2 sin t)
+    + cos(-b x1 sin t + b x2 cos t) + cos(b alpha x3)], t = 0.2 pi, V(y) = 6 - sum_j cos y_j."""
+    c, s = math.cos(theta), math.sin(theta)
+    P = beta * np.array([[1.0, 0.0, 0.0, c, -s, 0.0],
+                         [0.0, 1.0, 0.0, s, c, 0.0],
+                         [0.0, 0.0, 1.0, 0.0, 0.0, ALPHA_EX41]])
+    m, co = cosine_modes(6, -1.0, const=6.0)
+    return Problem("ex43", P, (K, K, K), (L, L, L), m, co, method=method,
+                   shift_round=shift_round, meta={"beta": beta, "theta": theta})
+
+
 def sweep_params(count: int, seed: int):
     """Batched moire sweep: eps ~ U[0.1,10], phases ~ U[0,2pi)^4, cutoff c ~ U[8,20].
 
