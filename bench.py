@@ -433,7 +433,7 @@ def run_ours(args):
     # its 1001 rows, then normalisation and density (iwf_field_normalize)
     evaluate = None
     if not args.no_evaluate:
-        xg = torch.from_numpy(W.physical_grid(2, rows=EVAL_ROWS)).cuda()
+        xg = torch.from_numpy(W.physical_grid(2, rows=args.eval_rows)).cuda()
         coef = x[0].contiguous()
         M = xg.shape[0]
         u = plan.evaluate(coef, xg)
@@ -455,8 +455,8 @@ def run_ours(args):
         evaluate = {
             "value": terms / (ms_ev * 1e-3), "unit": "coefficient-point terms/s",
             "ms": ms_ev, "points": M, "coefficients": plan.N,
-            "sample": f"{EVAL_ROWS} of 1001 rows of the [-50, 50]^2 grid, h = 0.1",
-            "full_grid_s": ms_ev * 1e-3 * 1001 / EVAL_ROWS,
+            "sample": f"{args.eval_rows} of 1001 rows of the [-50, 50]^2 grid, h = 0.1",
+            "full_grid_s": ms_ev * 1e-3 * 1001 / args.eval_rows,
             "normalize_ms": ms_norm,
             "roofline": {"bound": "alu", "achieved": tf_ev, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": tf_ev / FP64_PEAK_TFLOPS,
@@ -529,6 +529,8 @@ def main(argv=None):
                     help="skip the config-4 sweep subsample (batched vs one-by-one solves)")
     ap.add_argument("--no-evaluate", action="store_true",
                     help="skip the physical-space evaluation measurement")
+    ap.add_argument("--eval-rows", type=int, default=EVAL_ROWS,
+                    help="rows of the 1001 x 1001 observation grid the evaluation times")
     ap.add_argument("--solve-only", action="store_true",
                     help="run one eigensolve and print its timing (profiling aid)")
     ap.add_argument("--solve-run", default="iwfpm_f64", choices=[r[0] for r in SOLVE_RUNS])
