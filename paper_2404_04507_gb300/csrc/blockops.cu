@@ -601,8 +601,9 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
         // The angle t = tan(theta) only needs to be close (a rotation by a slightly wrong
         // angle leaves a tiny a_pq for the next sweep), so it is taken in FP32; c, s and the
         // unit phase e^{-i phi} must be orthonormal to working precision and are formed in
-        // FP64 from that t. This keeps the chain of dependent FP64 operations per round
-        // short: it is the latency of every round of the small Jacobi solves.
+        // FP64 from that t (double-float arithmetic would leave c^2 + s^2 - 1 near 1.5e-14,
+        // four times the FP64 rounding, which stalled the 32^4 solves). This keeps the chain
+        // of dependent FP64 operations per round short: it is the latency of every round.
         double c = 1.0, s = 0.0;
         double2 eph = make_double2(1.0, 0.0);   // e^{-i phi}
         int pp = p < q ? p : q, qq = p < q ? q : p;
@@ -661,9 +662,10 @@ __device__ void jacobi_eig(SmallShared& sh, int n) {
         }
       }
       __syncthreads();
-      // rows: A <- J^H A
+      // rows: A <- J^H A. Consecutive threads walk along a row (j fastest): rows start n
+      // entries of 16 B apart, so threads of one column in different rows would share banks.
       for (int e = tid; e < n * np; e += nt) {
-        const int j = e / np, k = e % np;
+        const int k = e / n, j = e % n;
         const int p = sh.rp[k];
         if (p < 0 || sh.rot_cs[k].z == 0.f) continue;
         const int q = sh.rq[k];
