@@ -155,7 +155,7 @@ def test_unknown_solver_precision_is_rejected(iwf):
 
 @pytest.mark.parametrize("precision", ["f64", "c64"])
 def test_qse3d_kronecker_spectrum(iwf, precision):
-    # the 3D QSE of the benchmark spec (P = [I3, sqrt2 I3], V = eps sum_j cos y_j + cos y_{j+3})
+    # the 3D QSE workload (P = [I3, sqrt2 I3], V = eps sum_j cos y_j + cos y_{j+3})
     # at K = L = 4 (8^6 grid, three-axis groups): the window, Lambda and V all factor over the
     # three spatial dimensions, so the exact spectrum is the Kronecker sum of three 1D problems
     # P = [1, sqrt2]; nev = 4 takes the ground state and its threefold degenerate cluster
