@@ -106,13 +106,19 @@ def ex41_v3(Ls=(128, 256, 512, 1024)):
     return [W.example_41(3.0, 8, L) for L in Ls], W.example_41(3.0, 10, 4096), 1
 
 
-def ex42(case: str = "I", Ls=(20, 30, 40, 50)):
-    """Example 4.2 case I (beta = 0.8 pi, theta = 0.2 pi), II (0.5 pi, 0.25 pi) or III
-    (0.5 pi, 0.2 pi): IWFPM K = 6 and PM K = 0.4L, 0.6L, 0.8L against IWFPM K = 10, L = 160."""
+def ex42(case: str = "I", Ls=None):
+    """Example 4.2. Case I (beta = 0.8 pi, theta = 0.2 pi): IWFPM K = 6 and PM K = 0.4L,
+    0.6L, 0.8L for L = 20 ... 50 against IWFPM K = 10, L = 160 (its table of errors). Cases
+    II (0.5 pi, 0.25 pi) and III (0.5 pi, 0.2 pi): IWFPM K = 8 for L = 128 ... 1024 (the DOFs
+    65536 ... 524288 of their tables; K = 8 is the window whose E_v matches the first printed
+    cell) against IWFPM K = 10, L = 4096."""
     beta, theta = {"I": (0.8, 0.2), "II": (0.5, 0.25), "III": (0.5, 0.2)}[case]
     beta, theta = beta * math.pi, theta * math.pi
+    if case != "I":
+        Ls = Ls or (128, 256, 512, 1024)
+        return [W.example_42(beta, theta, 8, L) for L in Ls], W.example_42(beta, theta, 10, 4096), 2
     wins = []
-    for L in Ls:
+    for L in Ls or (20, 30, 40, 50):
         wins.append(W.example_42(beta, theta, 6, L))
         for f in (0.4, 0.6, 0.8):
             wins.append(W.example_42(beta, theta, int(round(f * L)), L, method="pm"))
