@@ -428,6 +428,44 @@ def run_ours(args):
     stencil["note"] = (f"ablation, not the product path: direct convolution with the "
                        f"{nmodes_folded} folded modes; its cost grows with the number of modes")
 
+    # axes above 32 (shared-memory FFT, pass_long_kernel): the FP64 apply of a 16-vector
+    # block on the reference window of the paper's 1D accuracy table, Example 4.1 with PM
+    # K = 640, L = 1024 (a 1280 x 2048 grid, both axis groups long), against the FP64 peak
+    long_axis = None
+    if not args.no_long:
+        pl = W.example_41(2.5, 640, 1024, method="pm")
+        lplan = iwf.Plan(pl.P, pl.K, pl.L, method=pl.method)
+        lplan.set_potential(pl.modes, pl.coef)
+        ltune = lplan.autotune("f64", NVEC)
+        lx = torch.from_numpy(np.ascontiguousarray(W.random_block(lplan.N, NVEC, seed=7).T)).cuda()
+        ly = torch.empty_like(lx)
+        for _ in range(3):
+            lplan.apply(lx, ly)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nrep):
+            lplan.apply(lx, ly)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_l = e0.elapsed_time(e1) / nrep
+        lpts = float(lplan.N) * NVEC
+        lflops = 10.0 * math.log2(lplan.N) + 6.0
+        tf_l = lflops * lpts / (ms_l * 1e-3) / 1e12
+        l_ms, l_n = np.zeros(3), np.zeros(3)
+        for _ in range(3):
+            ms3, n3 = lplan.apply_profile(lx, ly)
+            l_ms += ms3
+            l_n += n3
+        long_axis = {"value": lpts / (ms_l * 1e-3), "unit": UNIT, "ms_per_step": ms_l,
+                     "grid": list(lplan.lens), "nvec": NVEC, "schedule": lplan.schedule("f64"),
+                     "pass_ms_per_apply": (l_ms / 3).round(4).tolist(),
+                     "roofline": {"bound": "alu", "achieved": tf_l, "peak": FP64_PEAK_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": tf_l / FP64_PEAK_TFLOPS,
+                                  "algorithmic_flops": f"{lflops:.0f} per point and vector "
+                                                       "(10 log2 N + 6)"}}
+        lplan.close()
+        del lx, ly
+
     # physical-space evaluation (iwf_evaluate) of one 32^4 coefficient vector on the 2D
     # observation grid of the accuracy study ([-50, 50]^2, h = 0.1), a bounded sample of 32 of
     # its 1001 rows, then normalisation and density (iwf_field_normalize)
@@ -504,7 +542,8 @@ def run_ours(args):
                    "parallelism": f"replicas{ws}", "schedule": tune,
                    "l2": "inputs 268 MB > 129 MB L2; no flush needed"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "c64_apply": c64, "stencil_ablation": stencil, "evaluate": evaluate,
+        "clocks": clk, "c64_apply": c64, "stencil_ablation": stencil, "long_axis": long_axis,
+        "evaluate": evaluate,
         "solve": solve,
         "sweep": sweep,
     }
@@ -527,6 +566,8 @@ def main(argv=None):
                     help="use the known tuned apply schedule instead of autotuning")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the config-4 sweep subsample (batched vs one-by-one solves)")
+    ap.add_argument("--no-long", action="store_true",
+                    help="skip the measurement of the long-axis (shared-memory FFT) apply")
     ap.add_argument("--no-evaluate", action="store_true",
                     help="skip the physical-space evaluation measurement")
     ap.add_argument("--eval-rows", type=int, default=EVAL_ROWS,
