@@ -146,6 +146,28 @@ class Plan:
                       "iwf_evaluate")
         return out
 
+    def evaluate_grid(self, coef, origin, step, count, out=None, stream=None):
+        """iwf_evaluate_grid: u on the uniform grid origin + (a step_0, b step_1), 0 <= a <
+        count[0], 0 <= b < count[1], for d = 2 and a diagonal P_I; returns a complex128 CUDA
+        vector of count[0]*count[1] values, the last axis fastest."""
+        torch = _torch()
+        if not (isinstance(coef, torch.Tensor) and coef.is_cuda and coef.dtype == torch.complex128
+                and coef.numel() == self.N and coef.is_contiguous()):
+            raise TypeError("coef must be a contiguous complex128 CUDA vector of length N")
+        o = (C.c_double * 2)(*[float(v) for v in origin])
+        h = (C.c_double * 2)(*[float(v) for v in step])
+        n = (C.c_int * 2)(*[int(v) for v in count])
+        M = int(count[0]) * int(count[1])
+        if out is None:
+            out = torch.empty(max(M, 0), dtype=torch.complex128, device=coef.device)
+        elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.complex128
+                  and out.numel() == M and out.is_contiguous()):
+            raise TypeError("out must be a contiguous complex128 CUDA vector of count[0]*count[1]")
+        self._c.check(self._c.iwf_evaluate_grid(self.handle, C.c_void_p(coef.data_ptr()), o, h, n,
+                                                C.c_void_p(out.data_ptr()), self._stream(stream)),
+                      "iwf_evaluate_grid")
+        return out
+
     @staticmethod
     def _check_field(u, name):
         torch = _torch()

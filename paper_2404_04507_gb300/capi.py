@@ -72,6 +72,8 @@ _PROTOS = {
     "iwf_apply_host": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_apply_stencil": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
     "iwf_evaluate": (_i, [_vp, _vp, _vp, _ll, _vp, _vp]),
+    "iwf_evaluate_grid": (_i, [_vp, _vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_int), _vp, _vp]),
     "iwf_field_normalize": (_i, [_vp, _vp, _ll, _ll, _vp, _vp, _vp]),
     "iwf_field_distance": (_i, [_vp, _vp, _vp, _ll, _vp, _vp]),
     "iwf_plan_autotune": (_i, [_vp, _i, _i, C.POINTER(C.c_double), C.POINTER(_i), _vp]),

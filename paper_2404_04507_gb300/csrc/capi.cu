@@ -293,6 +293,14 @@ iwf_status iwf_evaluate(iwf_plan* p, const void* coef, const double* x, long lon
   return evaluate_impl(p, coef, x, M, u, (cudaStream_t)stream);
 }
 
+iwf_status iwf_evaluate_grid(iwf_plan* p, const void* coef, const double* origin,
+                             const double* step, const int* count, void* u, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: NULL plan");
+  DeviceGuard guard(p->device);
+  return evaluate_grid_impl(p, coef, origin, step, count, u, (cudaStream_t)stream);
+}
+
 iwf_status iwf_field_normalize(iwf_plan* p, void* u, long long M, long long at, double* rho,
                                long long* argmax, void* stream) {
   clear_error();

@@ -195,6 +195,8 @@ iwf_status evaluate_impl(iwf_plan* p, const void* coef, const double* x, long lo
                          void* u, cudaStream_t stream);
 void release_host_pipeline(iwf_plan* p);
 iwf_status build_long_twiddles(iwf_plan* p);
+iwf_status evaluate_grid_impl(iwf_plan* p, const void* coef, const double* origin,
+                              const double* step, const int* count, void* u, cudaStream_t stream);
 iwf_status field_normalize_impl(iwf_plan* p, void* u, long long M, long long at, double* rho,
                                 long long* argmax, cudaStream_t stream);
 iwf_status field_distance_impl(iwf_plan* p, const void* u, const void* v, long long M,

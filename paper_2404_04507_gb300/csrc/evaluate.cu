@@ -15,6 +15,7 @@
 // consecutive slices. With one group the kernel writes u; with several each group writes a
 // partial sum and reduce_groups adds them in group order, so results do not depend on timing.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -127,6 +128,127 @@ __global__ void reduce_groups_kernel(const double2* __restrict__ part, long long
     s.y += v.y;
   }
   u[m] = s;
+}
+
+// ---- values on a uniform grid in 2D with a diagonal P_I (the observation grids of Sec. 4.2) --
+// With P_I = diag(p00, p11), (P k).x = x_0 (p00 k_1 + A_s) + x_1 (p11 k_2 + B_s), where
+// A_s = sum_{j>=2} P_0j k_j and B_s = sum_{j>=2} P_1j k_j depend only on the slice s (fixed
+// k_II). Within a slice k_I runs over the box [lo_1, lo_1 + 2K_1) x [lo_2, lo_2 + 2K_2), so the
+// slice's share of u on the grid x_0(a) = o_0 + a h_0, x_1(b) = o_1 + b h_1 is the product
+// E0_s C_s E1_s^T with C_s the slice's 2K_1 x 2K_2 coefficients, E0_s[a][i] =
+// exp(i x_0(a) (p00 (lo_1 + i) + A_s)) and E1_s[i][b] = exp(i x_1(b) (p11 (lo_2 + i) + B_s)).
+// Per slice and tile of kGT x kGT points: T = C_s E1_s^T (2K_1 x kGT), then u += E0_s T, i.e.
+// 2K_1 (1 + 2K_2 / kGT) complex multiply-adds per point instead of the 2K_1 2K_2 of direct
+// summation. Phase tables: one exact sincos per row or column and slice, then a recurrence of
+// at most 31 complex multiplications. FP64 throughout.
+constexpr int kGT = 64;              // output tile: kGT x kGT points
+constexpr int kGThreads = 256;
+constexpr int kGMaxLen = 32;         // largest 2K_j of the fast path
+constexpr int kGRows = kGThreads / kGT;          // 4 row groups of threads
+constexpr int kGAcc = kGT / kGRows;              // 16 accumulators per thread
+constexpr size_t kGSmem = sizeof(double2) * (size_t)(kGMaxLen * kGMaxLen + 3 * kGMaxLen * kGT);
+
+struct GridArgs {
+  Geom g;
+  double p00, p11;
+  double pa[IWF_MAX_N], pb[IWF_MAX_N];   // P_0j, P_1j of the k_II axes (index j)
+  double o0, o1, h0, h1;                 // grid origin and steps
+  int G0, G1;                            // points per axis
+  int tiles1;                            // tiles along axis 1
+  const int* lo;                         // MII x 2
+  const double2* coef;
+  long long o_per;
+  double2* out;                          // u (one group) or partials, group g at g * G0 * G1
+};
+
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__global__ void __launch_bounds__(kGThreads) evaluate_grid_kernel(GridArgs a) {
+  extern __shared__ __align__(16) unsigned char g_raw[];
+  double2* s_c = reinterpret_cast<double2*>(g_raw);          // [i0][i1], len1 stride
+  double2* s_e1 = s_c + kGMaxLen * kGMaxLen;                  // [i1][b]
+  double2* s_e0 = s_e1 + kGMaxLen * kGT;                      // [a][i0], kGMaxLen stride
+  double2* s_t = s_e0 + kGT * kGMaxLen;                       // [i0][b]
+  const Geom& g = a.g;
+  const int len0 = g.lens[0], len1 = g.lens[1];
+  const int MI = len0 * len1;
+  const int t = threadIdx.x;
+  const int tb = t % kGT, tr = t / kGT;                       // column and row group
+  const int ta0 = (blockIdx.x / a.tiles1) * kGT, tb0 = (blockIdx.x % a.tiles1) * kGT;
+  // grid coordinates of this thread's table row (t < kGT: column b = t; kGT <= t < 2 kGT:
+  // row a = t - kGT), with the same rounding as origin + index * step on the host
+  double xc = 0.0, zr = 1.0, zi = 0.0;                        // coordinate and step phase
+  if (t < 2 * kGT) {
+    xc = t < kGT ? __dadd_rn(a.o1, __dmul_rn((double)(tb0 + t), a.h1))
+                 : __dadd_rn(a.o0, __dmul_rn((double)(ta0 + t - kGT), a.h0));
+    sincos(xc * (t < kGT ? a.p11 : a.p00), &zi, &zr);
+  }
+  double2 acc[kGAcc];
+#pragma unroll
+  for (int j = 0; j < kGAcc; ++j) acc[j] = make_double2(0.0, 0.0);
+  const long long s0 = (long long)blockIdx.y * a.o_per;
+  const long long s1 = min(g.MII, s0 + a.o_per);
+  for (long long o = s0; o < s1; ++o) {
+    __syncthreads();                                          // previous slice's tables read
+    for (int e = t; e < MI; e += kGThreads) s_c[e] = a.coef[o * MI + e];
+    if (t < 2 * kGT) {
+      // slice constants: A_s or B_s from k_II = pos - L (C order, last axis fastest)
+      double sab = 0.0;
+      long long rem = o;
+      for (int j = g.n - 1; j >= 2; --j) {
+        const int len = g.lens[j];
+        const int kj = (int)(rem % len) - g.half[j];
+        rem /= len;
+        sab = fma(t < kGT ? a.pb[j] : a.pa[j], (double)kj, sab);
+      }
+      const bool col = t < kGT;
+      const int lo = a.lo[o * 2 + (col ? 1 : 0)];
+      const double freq = fma(col ? a.p11 : a.p00, (double)lo, sab);
+      double pr, pi;
+      sincos(xc * freq, &pi, &pr);
+      const int len = col ? len1 : len0;
+      for (int i = 0; i < len; ++i) {
+        if (col) s_e1[i * kGT + t] = make_double2(pr, pi);
+        else s_e0[(t - kGT) * kGMaxLen + i] = make_double2(pr, pi);
+        const double nr = fma(pr, zr, -pi * zi);
+        pi = fma(pr, zi, pi * zr);
+        pr = nr;
+      }
+    }
+    __syncthreads();
+    // T = C_s E1_s^T for this thread's column tb
+    for (int i0 = tr; i0 < len0; i0 += kGRows) {
+      double2 sum = make_double2(0.0, 0.0);
+      for (int i1 = 0; i1 < len1; ++i1) {
+        const double2 c = s_c[i0 * len1 + i1], e = s_e1[i1 * kGT + tb];
+        sum.x = fma(c.x, e.x, sum.x); sum.x = fma(-c.y, e.y, sum.x);
+        sum.y = fma(c.x, e.y, sum.y); sum.y = fma(c.y, e.x, sum.y);
+      }
+      s_t[i0 * kGT + tb] = sum;
+    }
+    __syncthreads();
+    // u += E0_s T for rows tr, tr + kGRows, ...
+    for (int i0 = 0; i0 < len0; ++i0) {
+      const double2 tv = s_t[i0 * kGT + tb];
+#pragma unroll
+      for (int j = 0; j < kGAcc; ++j) {
+        const double2 e = s_e0[(tr + kGRows * j) * kGMaxLen + i0];
+        acc[j].x = fma(e.x, tv.x, acc[j].x); acc[j].x = fma(-e.y, tv.y, acc[j].x);
+        acc[j].y = fma(e.x, tv.y, acc[j].y); acc[j].y = fma(e.y, tv.x, acc[j].y);
+      }
+    }
+  }
+  const long long M = (long long)a.G0 * a.G1;
+  const int b = tb0 + tb;
+  if (b < a.G1) {
+#pragma unroll
+    for (int j = 0; j < kGAcc; ++j) {
+      const int ra = ta0 + tr + kGRows * j;
+      if (ra < a.G0) a.out[(long long)blockIdx.y * M + (long long)ra * a.G1 + b] = acc[j];
+    }
+  }
 }
 
 // ---- normalised fields, density and E_f (Sec. 4.2) ----
@@ -317,6 +439,81 @@ iwf_status field_distance_impl(iwf_plan* p, const void* u, const void* v, long l
   IWF_CUDA(cudaGetLastError());
   count_launch();
   if (M > 0) count_launch();
+  return IWF_OK;
+}
+
+}  // namespace iwf
+
+namespace iwf {
+
+iwf_status evaluate_grid_impl(iwf_plan* p, const void* coef, const double* origin,
+                              const double* step, const int* count, void* u,
+                              cudaStream_t stream) {
+  const Geom& g = p->g;
+  if (!origin || !step || !count) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: null argument");
+  if (g.d != 2 || g.n < 3)
+    return fail(IWF_ERR_UNSUPPORTED, "iwf_evaluate_grid: needs d = 2 (use iwf_evaluate)");
+  if (p->P[1] != 0.0 || p->P[g.n] != 0.0)
+    return fail(IWF_ERR_UNSUPPORTED, "iwf_evaluate_grid: P_I not diagonal (use iwf_evaluate)");
+  if (g.lens[0] > kGMaxLen || g.lens[1] > kGMaxLen)
+    return fail(IWF_ERR_UNSUPPORTED, "iwf_evaluate_grid: 2K above 32 (use iwf_evaluate)");
+  if (count[0] < 0 || count[1] < 0) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: count < 0");
+  for (int r = 0; r < 2; ++r)
+    if (!std::isfinite(origin[r]) || !std::isfinite(step[r]))
+      return fail(IWF_ERR_NONFINITE, "iwf_evaluate_grid: non-finite origin or step");
+  const long long M = (long long)count[0] * count[1];
+  if (M == 0) return IWF_OK;
+  if (!coef || !u) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: null pointer");
+  const long long tiles0 = (count[0] + kGT - 1) / kGT, tiles1 = (count[1] + kGT - 1) / kGT;
+  if (tiles0 * tiles1 > 2147483647LL) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: grid too large");
+  const long long tiles = tiles0 * tiles1;
+  int sms = 0;
+  IWF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  long long groups = std::max(1LL, (2LL * sms + tiles - 1) / tiles);
+  groups = std::min(groups, g.MII);
+  groups = std::min(groups, std::max(1LL, (long long)(kEvalPartMax / (16 * (size_t)M))));
+  groups = std::min(groups, 65535LL);
+  const long long o_per = (g.MII + groups - 1) / groups;
+  groups = (g.MII + o_per - 1) / o_per;
+  GridArgs a{};
+  a.g = g;
+  a.p00 = p->P[0];
+  a.p11 = p->P[g.n + 1];
+  for (int j = 2; j < g.n; ++j) { a.pa[j] = p->P[j]; a.pb[j] = p->P[g.n + j]; }
+  a.o0 = origin[0]; a.o1 = origin[1]; a.h0 = step[0]; a.h1 = step[1];
+  a.G0 = count[0]; a.G1 = count[1];
+  a.tiles1 = (int)tiles1;
+  a.lo = p->d_lo;
+  a.coef = reinterpret_cast<const double2*>(coef);
+  a.o_per = o_per;
+  if (groups == 1) {
+    a.out = reinterpret_cast<double2*>(u);
+  } else {
+    const size_t need = (size_t)groups * (size_t)M * sizeof(double2);
+    if (need > p->eval_part_bytes) {
+      cudaFree(p->d_eval_part);
+      p->d_eval_part = nullptr;
+      p->eval_part_bytes = 0;
+      IWF_CUDA(cudaMalloc(&p->d_eval_part, need));
+      p->eval_part_bytes = need;
+    }
+    a.out = p->d_eval_part;
+  }
+  static bool attr[64] = {};
+  if (p->device >= 0 && p->device < 64 && !attr[p->device]) {
+    IWF_CUDA(cudaFuncSetAttribute(evaluate_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kGSmem));
+    attr[p->device] = true;
+  }
+  evaluate_grid_kernel<<<dim3((unsigned)tiles, (unsigned)groups), kGThreads, kGSmem, stream>>>(a);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  if (groups > 1) {
+    reduce_groups_kernel<<<(unsigned)((M + kEvalThreads - 1) / kEvalThreads), kEvalThreads, 0,
+                           stream>>>(p->d_eval_part, M, (int)groups, reinterpret_cast<double2*>(u));
+    IWF_CUDA(cudaGetLastError());
+    count_launch();
+  }
   return IWF_OK;
 }
 

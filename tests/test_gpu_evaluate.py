@@ -211,3 +211,61 @@ def test_ground_state_field_and_density_end_to_end(iwf, phases):
     r = rho.cpu().numpy()
     assert abs(r.max() - 1.0) <= 1e-7 and abs(r[i] - 1.0) <= 4 * EPS
     assert np.max(np.abs(r - T.density(want))) <= 2e-6
+
+
+GRID_PROBS = {
+    "moire_small": PROBS["moire_small"],
+    "moire_ragged": PROBS["moire_ragged"],
+    "pm_moire": PROBS["pm_moire"],
+    "ex42": W.example_42(0.8 * np.pi, 0.2 * np.pi, 6, 20),
+    "random_grid_pot": PROBS["random_grid_pot"],
+}
+
+
+def _grid_points(origin, step, count):
+    x0 = origin[0] + np.arange(count[0]) * step[0]
+    x1 = origin[1] + np.arange(count[1]) * step[1]
+    return np.ascontiguousarray(np.stack(np.meshgrid(x0, x1, indexing="ij"), -1).reshape(-1, 2))
+
+
+@pytest.mark.parametrize("name", sorted(GRID_PROBS))
+def test_evaluate_grid_matches_oracle(iwf, name):
+    # a 70 x 130 grid: 2 x 3 tiles of 64 points, ragged in both directions
+    pb = GRID_PROBS[name]
+    plan, win, c = _setup(iwf, pb)
+    origin, step, count = (-50.0, -50.0), (0.1, 0.1), (70, 130)
+    got = plan.evaluate_grid(torch.from_numpy(c).cuda(), origin, step, count)
+    torch.cuda.synchronize()
+    x = _grid_points(origin, step, count)
+    want = T.evaluate_quasi(win, c, x)
+    assert np.max(np.abs(got.cpu().numpy() - want)) <= _tol(win, c, x)
+
+
+def test_evaluate_grid_equals_direct_full_size(iwf):
+    # the 32^4 window on 200 x 300 points of the 2D observation grid: the separable products
+    # against direct summation, and the oracle on a sample
+    pb = W.config_moire(eps=0.5)
+    plan, win, c = _setup(iwf, pb)
+    origin, step, count = (-50.0, -50.0), (0.1, 0.1), (200, 300)
+    ct = torch.from_numpy(c).cuda()
+    got = plan.evaluate_grid(ct, origin, step, count).cpu().numpy()
+    x = _grid_points(origin, step, count)
+    direct = plan.evaluate(ct, torch.from_numpy(x).cuda()).cpu().numpy()
+    tol = _tol(win, c, x)
+    assert np.max(np.abs(got - direct)) <= 2 * tol
+    pick = np.random.default_rng(3).choice(len(x), 12, replace=False)
+    assert np.max(np.abs(got[pick] - T.evaluate_quasi(win, c, x[pick]))) <= tol
+
+
+def test_evaluate_grid_unsupported_and_empty(iwf):
+    from paper_2404_04507_gb300 import capi
+    skew = W.Problem("skew", np.array([[1.0, 0.3, 0.7], [0.2, 1.0, 0.5]]), (2, 2), (2,),
+                     *W.cosine_modes(3, 1.0))
+    for pb in (PROBS["qse1d"], skew, PROBS["qse3d_small"]):   # d = 1, P_I not diagonal, d = 3
+        plan, win, c = _setup(iwf, pb)
+        with pytest.raises(capi.IwfError) as e:
+            plan.evaluate_grid(torch.from_numpy(c).cuda(), (0.0, 0.0), (0.1, 0.1), (4, 4))
+        assert e.value.status == -10
+    plan, win, c = _setup(iwf, PROBS["moire_small"])
+    out = plan.evaluate_grid(torch.from_numpy(c).cuda(), (0.0, 0.0), (0.1, 0.1), (0, 7))
+    assert out.numel() == 0
