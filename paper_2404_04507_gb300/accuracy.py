@@ -49,23 +49,42 @@ def ground_state(pb, tol: float = 1e-10, precision: str = "f64", block: int = 16
             "resid": float(res[0]), "seconds": time.perf_counter() - t0}
 
 
-def observe(gs, x, at=None):
+def observe(gs, x, at=None, grid=None):
     """u_0 on the points x (a float64 CUDA tensor (M, d)), normalised in place at point `at`
-    (None: its own first point of largest modulus). Returns (u, index of that point)."""
-    u = gs["plan"].evaluate(gs["coef"], x)
-    _, idx = gs["plan"].normalize_field(u, at=at, want_rho=False)
+    (None: its own first point of largest modulus). Returns (u, index of that point). With
+    grid = (origin, step, count) describing the same points as a uniform 2D grid, the values
+    come from iwf_evaluate_grid where the plan allows it (d = 2, diagonal P_I, 2K <= 32)."""
+    from .capi import IwfError
+    plan = gs["plan"]
+    u = None
+    if grid is not None:
+        try:
+            u = plan.evaluate_grid(gs["coef"], *grid)
+        except IwfError as e:
+            if e.status != -10:
+                raise
+    if u is None:
+        u = plan.evaluate(gs["coef"], x)
+    _, idx = plan.normalize_field(u, at=at, want_rho=False)
     return u, int(idx.item())
 
 
 def study(windows, reference, d: int, tol: float = 1e-10, precision: str = "f64",
-          grid_rows: int | None = None, maxit: int = 5000, fields: bool = True):
+          grid_rows: int | None = None, maxit: int = 5000, fields: bool = True,
+          use_grid: bool = True):
     """E_v and E_f of every problem in `windows` against `reference` on the observation
-    grid of dimension d (the first `grid_rows` rows of it if given; fields=False skips E_f).
-    Yields one dict per window, the reference first."""
+    grid of dimension d (the first `grid_rows` rows of it if given; fields=False skips E_f;
+    use_grid=False evaluates every field by direct summation). Yields one dict per window,
+    the reference first."""
     torch = _torch()
     x = torch.from_numpy(W.physical_grid(d, rows=grid_rows)).cuda() if fields else None
+    grid = None
+    if fields and use_grid and d == 2:
+        hw = 5.0 * 10.0 ** (3 - d)
+        cnt = int(round(2 * hw / 0.1)) + 1
+        grid = ((-hw, -hw), (0.1, 0.1), (min(cnt, grid_rows or cnt), cnt))
     ref = ground_state(reference, tol, precision, maxit=maxit)
-    u_ref, i_ref = observe(ref, x) if fields else (None, None)
+    u_ref, i_ref = observe(ref, x, grid=grid) if fields else (None, None)
     yield {"name": reference.name, "method": reference.method, "K": list(reference.K),
            "L": list(reference.L), "dof": ref["dof"], "E0": ref["E0"], "iters": ref["iters"],
            "resid": ref["resid"], "converged": ref["converged"], "seconds": ref["seconds"],
@@ -74,7 +93,7 @@ def study(windows, reference, d: int, tol: float = 1e-10, precision: str = "f64"
         gs = ground_state(pb, tol, precision, maxit=maxit)
         ef = None
         if fields:
-            u, _ = observe(gs, x, at=i_ref)
+            u, _ = observe(gs, x, at=i_ref, grid=grid)
             ef = float(gs["plan"].field_distance(u, u_ref).item())
         yield {"name": pb.name, "method": pb.method, "K": list(pb.K), "L": list(pb.L),
                "dof": gs["dof"], "E0": gs["E0"], "iters": gs["iters"], "resid": gs["resid"],

@@ -85,3 +85,20 @@ def test_table4_example41_localised_eigenvalue_errors(acc):
     for method, K, L, ev in read_golden("table4_ex41_v3_errors.txt"):
         r = rows[(method, int(K), int(L))]
         assert _close(r["E_v"], float(ev), 0.05), (K, L, r["E_v"], ev)
+
+
+def test_grid_and_direct_fields_agree(acc):
+    # E_f of Example 4.2 windows on 8 rows of the 2D observation grid: the separable products
+    # (iwf_evaluate_grid) and direct summation (iwf_evaluate) give the same errors; the PM
+    # window with 2K = 40 > 32 takes the direct path in both runs
+    import math
+    from paper_2404_04507_gb300 import workloads as W
+    beta, theta = 0.8 * math.pi, 0.2 * math.pi
+    wins = [W.example_42(beta, theta, 6, 20), W.example_42(beta, theta, 20, 20, method="pm")]
+    ref = W.example_42(beta, theta, 6, 30)
+    a = [r for r in acc.study(wins, ref, 2, grid_rows=8) if not r.get("reference")]
+    b = [r for r in acc.study(wins, ref, 2, grid_rows=8, use_grid=False)
+         if not r.get("reference")]
+    for ra, rb in zip(a, b):
+        assert ra["E0"] == rb["E0"]
+        assert abs(ra["E_f"] - rb["E_f"]) <= 1e-12
