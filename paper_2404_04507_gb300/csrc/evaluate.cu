@@ -137,16 +137,18 @@ __global__ void reduce_groups_kernel(const double2* __restrict__ part, long long
 // slice's share of u on the grid x_0(a) = o_0 + a h_0, x_1(b) = o_1 + b h_1 is the product
 // E0_s C_s E1_s^T with C_s the slice's 2K_1 x 2K_2 coefficients, E0_s[a][i] =
 // exp(i x_0(a) (p00 (lo_1 + i) + A_s)) and E1_s[i][b] = exp(i x_1(b) (p11 (lo_2 + i) + B_s)).
-// Per slice and tile of kGT x kGT points: T = C_s E1_s^T (2K_1 x kGT), then u += E0_s T, i.e.
-// 2K_1 (1 + 2K_2 / kGT) complex multiply-adds per point instead of the 2K_1 2K_2 of direct
+// Per slice and tile of kGA x kGT points: T = C_s E1_s^T (2K_1 x kGT), then u += E0_s T, i.e.
+// 2K_1 (1 + 2K_2 / kGA) complex multiply-adds per point instead of the 2K_1 2K_2 of direct
 // summation. Phase tables: one exact sincos per row or column and slice, then a recurrence of
 // at most 31 complex multiplications. FP64 throughout.
-constexpr int kGT = 64;              // output tile: kGT x kGT points
-constexpr int kGThreads = 256;
+constexpr int kGT = 64;              // output tile: kGA rows x kGT columns
+constexpr int kGA = 128;
+constexpr int kGThreads = 512;
 constexpr int kGMaxLen = 32;         // largest 2K_j of the fast path
-constexpr int kGRows = kGThreads / kGT;          // 4 row groups of threads
-constexpr int kGAcc = kGT / kGRows;              // 16 accumulators per thread
-constexpr size_t kGSmem = sizeof(double2) * (size_t)(kGMaxLen * kGMaxLen + 3 * kGMaxLen * kGT);
+constexpr int kGRows = kGThreads / kGT;          // 8 row groups of threads
+constexpr int kGAcc = kGA / kGRows;              // 16 accumulators per thread
+constexpr size_t kGSmem =
+    sizeof(double2) * (size_t)(kGMaxLen * kGMaxLen + 2 * kGMaxLen * kGT + kGA * kGMaxLen);
 
 struct GridArgs {
   Geom g;
@@ -165,22 +167,22 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-__global__ void __launch_bounds__(kGThreads) evaluate_grid_kernel(GridArgs a) {
+__global__ void __launch_bounds__(kGThreads, 1) evaluate_grid_kernel(GridArgs a) {
   extern __shared__ __align__(16) unsigned char g_raw[];
   double2* s_c = reinterpret_cast<double2*>(g_raw);          // [i0][i1], len1 stride
   double2* s_e1 = s_c + kGMaxLen * kGMaxLen;                  // [i1][b]
   double2* s_e0 = s_e1 + kGMaxLen * kGT;                      // [a][i0], kGMaxLen stride
-  double2* s_t = s_e0 + kGT * kGMaxLen;                       // [i0][b]
+  double2* s_t = s_e0 + kGA * kGMaxLen;                       // [i0][b]
   const Geom& g = a.g;
   const int len0 = g.lens[0], len1 = g.lens[1];
   const int MI = len0 * len1;
   const int t = threadIdx.x;
   const int tb = t % kGT, tr = t / kGT;                       // column and row group
-  const int ta0 = (blockIdx.x / a.tiles1) * kGT, tb0 = (blockIdx.x % a.tiles1) * kGT;
-  // grid coordinates of this thread's table row (t < kGT: column b = t; kGT <= t < 2 kGT:
+  const int ta0 = (blockIdx.x / a.tiles1) * kGA, tb0 = (blockIdx.x % a.tiles1) * kGT;
+  // grid coordinates of this thread's table row (t < kGT: column b = t; kGT <= t < kGT + kGA:
   // row a = t - kGT), with the same rounding as origin + index * step on the host
   double xc = 0.0, zr = 1.0, zi = 0.0;                        // coordinate and step phase
-  if (t < 2 * kGT) {
+  if (t < kGT + kGA) {
     xc = t < kGT ? __dadd_rn(a.o1, __dmul_rn((double)(tb0 + t), a.h1))
                  : __dadd_rn(a.o0, __dmul_rn((double)(ta0 + t - kGT), a.h0));
     sincos(xc * (t < kGT ? a.p11 : a.p00), &zi, &zr);
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kGThreads) evaluate_grid_kernel(GridArgs a) {
   for (long long o = s0; o < s1; ++o) {
     __syncthreads();                                          // previous slice's tables read
     for (int e = t; e < MI; e += kGThreads) s_c[e] = a.coef[o * MI + e];
-    if (t < 2 * kGT) {
+    if (t < kGT + kGA) {
       // slice constants: A_s or B_s from k_II = pos - L (C order, last axis fastest)
       double sab = 0.0;
       long long rem = o;
@@ -464,12 +466,13 @@ iwf_status evaluate_grid_impl(iwf_plan* p, const void* coef, const double* origi
   const long long M = (long long)count[0] * count[1];
   if (M == 0) return IWF_OK;
   if (!coef || !u) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: null pointer");
-  const long long tiles0 = (count[0] + kGT - 1) / kGT, tiles1 = (count[1] + kGT - 1) / kGT;
+  const long long tiles0 = (count[0] + kGA - 1) / kGA, tiles1 = (count[1] + kGT - 1) / kGT;
   if (tiles0 * tiles1 > 2147483647LL) return fail(IWF_ERR_ARG, "iwf_evaluate_grid: grid too large");
   const long long tiles = tiles0 * tiles1;
   int sms = 0;
   IWF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  long long groups = std::max(1LL, (2LL * sms + tiles - 1) / tiles);
+  // one CTA per SM: about four waves of slice groups
+  long long groups = std::max(1LL, (4LL * sms + tiles - 1) / tiles);
   groups = std::min(groups, g.MII);
   groups = std::min(groups, std::max(1LL, (long long)(kEvalPartMax / (16 * (size_t)M))));
   groups = std::min(groups, 65535LL);
