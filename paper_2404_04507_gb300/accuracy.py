@@ -78,11 +78,7 @@ def study(windows, reference, d: int, tol: float = 1e-10, precision: str = "f64"
     the reference first."""
     torch = _torch()
     x = torch.from_numpy(W.physical_grid(d, rows=grid_rows)).cuda() if fields else None
-    grid = None
-    if fields and use_grid and d == 2:
-        hw = 5.0 * 10.0 ** (3 - d)
-        cnt = int(round(2 * hw / 0.1)) + 1
-        grid = ((-hw, -hw), (0.1, 0.1), (min(cnt, grid_rows or cnt), cnt))
+    grid = W.grid_descriptor(d, grid_rows) if (fields and use_grid and d == 2) else None
     ref = ground_state(reference, tol, precision, maxit=maxit)
     u_ref, i_ref = observe(ref, x, grid=grid) if fields else (None, None)
     yield {"name": reference.name, "method": reference.method, "K": list(reference.K),

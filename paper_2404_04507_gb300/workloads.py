@@ -188,6 +188,15 @@ def physical_grid(d: int, h: float = 0.1, half_width: float | None = None,
     return np.ascontiguousarray(np.stack([g.ravel() for g in mesh], axis=1))
 
 
+def grid_descriptor(d: int, rows: int | None = None, h: float = 0.1):
+    """(origin, step, count) of the 2D observation grid [-5a, 5a]^2, a = 10^(3-d), step h, as a
+    uniform-grid evaluation takes it: the same points, in the same order, as
+    physical_grid(d, h, rows=rows)."""
+    hw = 5.0 * 10.0 ** (3 - d)
+    cnt = int(round(2 * hw / h)) + 1
+    return (-hw, -hw), (h, h), (min(cnt, rows or cnt), cnt)
+
+
 def random_P(d: int, n: int, seed: int) -> np.ndarray:
     """P = [I_d, Q0] with Q0 ~ U(-1.5, 1.5): generic irrational-looking entries."""
     rng = np.random.default_rng(seed)

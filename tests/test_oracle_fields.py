@@ -95,3 +95,15 @@ def test_two_mode_field_on_the_1d_grid():
     assert np.max(np.abs(u - (np.exp(1j * xs) + np.exp(1j * math.sqrt(5.0) * xs)) / 2)) < 1e-12
     rho = T.density(u)
     assert np.max(np.abs(rho - (1 + np.cos((math.sqrt(5.0) - 1) * xs)) / 2)) < 1e-12
+
+
+def test_grid_descriptor_names_the_observation_grid():
+    # the (origin, step, count) handed to the separable grid evaluation expands, with the
+    # kernel's own rounding (origin + index * step), to exactly the observation grid's points
+    for rows in (None, 8):
+        (o0, o1), (h0, h1), (c0, c1) = W.grid_descriptor(2, rows)
+        pts = W.physical_grid(2, rows=rows)
+        x0 = o0 + np.arange(c0) * h0
+        x1 = o1 + np.arange(c1) * h1
+        mesh = np.stack(np.meshgrid(x0, x1, indexing="ij"), -1).reshape(-1, 2)
+        assert mesh.shape == pts.shape and np.array_equal(mesh, pts)
