@@ -2,7 +2,8 @@
 
 Each lifted potential, summed from its Fourier modes by the oracle, must equal the printed
 parent function V(y) at random lifted points, and its restriction v(x) = V(P^T x) the printed
-physical potential; each P must be the printed projection matrix.
+physical potential; each P must be the printed projection matrix. The accuracy studies run on
+the GPU must list exactly the windows of the printed tables they are compared with.
 """
 import math
 
@@ -56,3 +57,25 @@ def test_example_43():
            beta * np.array([[1.0, 0.0, 0.0, c, -s, 0.0],
                             [0.0, 1.0, 0.0, s, c, 0.0],
                             [0.0, 0.0, 1.0, 0.0, 0.0, a]]))
+
+
+def test_accuracy_studies_cover_the_golden_tables():
+    # the GPU studies run exactly the windows the printed tables list, against the references
+    # the tables name (the library is built first: importing the package loads it)
+    from paper_2404_04507_gb300 import build
+    build.build()
+    from paper_2404_04507_gb300 import accuracy as A
+    from conftest import read_golden
+
+    def keys(wins):
+        return {(p.method, int(p.K[0]), int(p.L[0])) for p in wins}
+
+    for study, golden, ref in ((A.ex41_v25(), "table2_ex41_errors.txt", ("pm", 640, 1024)),
+                               (A.ex41_v3(), "table4_ex41_v3_errors.txt", ("iwfpm", 10, 4096)),
+                               (A.ex42("I"), "table5_ex42_errors.txt", ("iwfpm", 10, 160))):
+        wins, reference, d = study
+        rows = {(r[0], int(r[1]), int(r[2])) for r in read_golden(golden)}
+        assert rows == keys(wins), golden
+        assert (reference.method, int(reference.K[0]), int(reference.L[0])) == ref
+    wins, reference, d = A.ex41_v25(reference="iwfpm96")
+    assert (reference.method, int(reference.K[0]), int(reference.L[0])) == ("iwfpm", 5, 96)
