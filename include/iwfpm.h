@@ -178,8 +178,10 @@ typedef struct {
  *   info   host (may be NULL).
  * The call allocates its workspace (about 12 blocks of N*block complex values) and
  * synchronises `stream` before returning.
- * Errors: IWF_ERR_ARG, IWF_ERR_ALLOC, IWF_ERR_CUDA, IWF_ERR_NONFINITE, IWF_ERR_BREAKDOWN,
- * IWF_ERR_NOCONV (outputs then hold the last iterate).
+ * Errors: IWF_ERR_ARG, IWF_ERR_ALLOC, IWF_ERR_CUDA, IWF_ERR_NONFINITE (a NaN or Inf in X0,
+ * checked on the device before the first iteration, or a non-finite residual), IWF_ERR_TIMEOUT
+ * (an apply gave up waiting for a copy, read at the per-iteration synchronisation),
+ * IWF_ERR_BREAKDOWN, IWF_ERR_NOCONV (outputs then hold the last iterate).
  */
 iwf_status iwf_eigensolve(iwf_plan* plan, const iwf_solve_opts* opts, const void* X0,
                           double* evals, void* evecs, double* resid, iwf_solve_info* info,
@@ -424,6 +426,28 @@ long long iwf_kernel_launches(void);
  */
 iwf_status iwf_apply_noalloc(iwf_plan* plan, int precision, const void* psi, void* hpsi,
                              int nvec, void* stream);
+
+/*
+ * Device-side failures of the apply. The pipelined pass C (complex-float pencil path) waits on
+ * its bulk copies with bounded waits; a wait that runs out records IWF_ERR_TIMEOUT in the
+ * plan's device error word and the kernel returns without storing the rest of H~ psi
+ * (failure detection; the paper has no counterpart). iwf_apply and
+ * iwf_apply_noalloc only enqueue work, so they cannot see the word; it is read and cleared at
+ * the plan's next synchronisation point: iwf_apply_host, iwf_apply_profile, iwf_eigensolve
+ * and iwf_batch_eigensolve (every iteration), or this call.
+ * iwf_plan_check synchronises `stream` and returns IWF_ERR_TIMEOUT (clearing the word) when
+ * an apply on the plan gave up waiting since the last check, IWF_OK otherwise.
+ */
+iwf_status iwf_plan_check(iwf_plan* plan, void* stream);
+
+/*
+ * Bound on the main waits of the plan's pipelined passes, in try_wait rounds (rounds < 0: the
+ * default of 2^20, far above any real copy latency). A fault-injection knob for tests: with 0
+ * every pipelined pass gives up at its first wait, so the apply reports IWF_ERR_TIMEOUT at the
+ * next check. The drain of copies already in flight keeps the default bound, so the kernel
+ * still lets them land before it exits.
+ */
+iwf_status iwf_plan_set_wait_limit(iwf_plan* plan, long long rounds);
 
 #ifdef __cplusplus
 }

@@ -281,6 +281,17 @@ class Plan:
         return {"threads": out[0], "tile_kb": out[1], "chunk_mb": out[2],
                 "path": names[out[3]]}
 
+    def check(self, stream=None):
+        """iwf_plan_check: raises IwfError (IWF_ERR_TIMEOUT) if an apply on this plan gave up
+        waiting since the last check; synchronises the stream."""
+        self._c.check(self._c.iwf_plan_check(self.handle, self._stream(stream)), "iwf_plan_check")
+
+    def set_wait_limit(self, rounds):
+        """iwf_plan_set_wait_limit: try_wait rounds of each main wait of the pipelined passes
+        (negative: the default)."""
+        self._c.check(self._c.iwf_plan_set_wait_limit(self.handle, int(rounds)),
+                      "iwf_plan_set_wait_limit")
+
     def apply_profile(self, psi, out, stream=None):
         """iwf_apply_profile: same result as apply(); returns (pass_ms[3], launches[3])."""
         nvec = self._check_block(psi)

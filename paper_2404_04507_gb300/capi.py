@@ -98,6 +98,8 @@ _PROTOS = {
                           C.c_ulonglong, C.POINTER(C.c_float), _vp]),
     "iwf_ws_embed": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
     "iwf_ws_phase": (_i, [_vp, _i, _i, C.POINTER(C.c_double), _i, _vp, _vp]),
+    "iwf_plan_check": (_i, [_vp, _vp]),
+    "iwf_plan_set_wait_limit": (_i, [_vp, _ll]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _fn = getattr(lib, _name)

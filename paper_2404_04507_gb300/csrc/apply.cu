@@ -436,6 +436,7 @@ struct PencilArgs {
   long long ld;             // N, elements between vectors
   long long MI, MII;        // LI^2, LII^2
   int vec_base;
+  long long spin;           // pipelined pass C: try_wait rounds of each main wait
 };
 
 template <typename T> constexpr int wave_lanes() { return sizeof(T) == 4 ? 16 : 8; }
@@ -576,9 +577,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for phase `parity` of the barrier; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long r = 0; r < kSpinRounds; ++r)
+// Bounded wait for phase `parity` of the barrier (at most `rounds` try_wait rounds); false
+// when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long rounds = kSpinRounds) {
+  for (long long r = 0; r < rounds; ++r)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -681,7 +684,7 @@ __global__ void __launch_bounds__(WARPS * 32) pencil_c_pipe_kernel(PencilArgs a,
     const long long o = (u % upv) * SPW + s;          // slice of this lane
     const int lo0 = a.lo[2 * o], lo1 = a.lo[2 * o + 1];  // issued before the wait, which hides them
     const int st = k % STAGES;
-    ok = mbar_wait(smem_addr(&bars[warp][st]), (uint32_t)((k / STAGES) & 1));
+    ok = mbar_wait(smem_addr(&bars[warp][st]), (uint32_t)((k / STAGES) & 1), a.spin);
     if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
     V2* U = stages + st * UNIT + s * LL;               // this lane's slice in the stage
     const int off0 = roll_of(lo0, L), off1 = roll_of(lo1, L);
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(WARPS * 32) pencil_c_pipe_kernel(PencilArgs a,
 #pragma unroll
       for (int i = 0; i < L; ++i) { const V2 v = U[i * L + (p ^ i)]; xr[i] = v.x; xi[i] = v.y; }
       Dft<L, -1, T>::run(xr, xi);
-      ok = mbar_wait(smem_addr(&bars[warp][STAGES]), (uint32_t)(k & 1));
+      ok = mbar_wait(smem_addr(&bars[warp][STAGES]), (uint32_t)(k & 1), a.spin);
       if (__any_sync(0xffffffffu, !ok)) { ok = false; break; }
       psi_pending = false;
       // grid -> window order, + Lambda psi at the same window positions
@@ -723,7 +726,8 @@ __global__ void __launch_bounds__(WARPS * 32) pencil_c_pipe_kernel(PencilArgs a,
     }
   }
   if (!ok) {
-    // record the timeout, then give the copies still in flight a bounded time to land
+    // record the timeout, then give the copies still in flight a bounded time to land (the
+    // full bound, whatever a.spin is)
     if (lane == 0) atomicExch(err, kApplyTimeout);
     if (psi_pending) mbar_wait(smem_addr(&bars[warp][STAGES]), (uint32_t)(k & 1));
     for (; k < kp; ++k) mbar_wait(smem_addr(&bars[warp][k % STAGES]), (uint32_t)((k / STAGES) & 1));
@@ -840,12 +844,17 @@ __global__ void __launch_bounds__(C * L) pencil_b_kernel(PencilArgs a) {
   }
 }
 
+// Per-device flag for the twiddle tables, guarded by a mutex so that first calls from several
+// host threads fill the tables once. The flags assume the device's primary context is never
+// reset while the library is loaded.
+std::mutex g_tw_mu;
 bool g_tw_ready[64] = {};
 
 iwf_status init_twiddles(int device) {
+  std::lock_guard<std::mutex> lock(g_tw_mu);
   if (device >= 0 && device < 64 && g_tw_ready[device]) return IWF_OK;
-  static double2 h64[kTwTotal];
-  static float2 h32[kTwTotal];
+  std::vector<double2> h64(kTwTotal);
+  std::vector<float2> h32(kTwTotal);
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int len = 1; len <= IWF_MAX_LEN; ++len) {
     for (int j = 0; j < len; ++j) {
@@ -859,8 +868,8 @@ iwf_status init_twiddles(int device) {
       h32[tw_off(len) + j] = make_float2((float)c, (float)s);
     }
   }
-  IWF_CUDA(cudaMemcpyToSymbol(c_tw64, h64, sizeof(h64)));
-  IWF_CUDA(cudaMemcpyToSymbol(c_tw32, h32, sizeof(h32)));
+  IWF_CUDA(cudaMemcpyToSymbol(c_tw64, h64.data(), sizeof(double2) * kTwTotal));
+  IWF_CUDA(cudaMemcpyToSymbol(c_tw32, h32.data(), sizeof(float2) * kTwTotal));
   if (device >= 0 && device < 64) g_tw_ready[device] = true;
   return IWF_OK;
 }
@@ -1168,6 +1177,7 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     // pencil geometry: N = LI^2 LII^2 <= 2^20, so in-vector offsets fit in int
     PencilArgs pa{};
     pa.lo = p->d_lo; pa.pot = pot; pa.ld = g.N; pa.MI = g.MI; pa.MII = g.MII;
+    pa.spin = p->wait_rounds >= 0 ? p->wait_rounds : kSpinRounds;
     for (int v0 = 0; v0 < nvec; v0 += chunk) {
       const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
       pa.vec_base = v0;
@@ -1327,6 +1337,7 @@ iwf_status build_long_twiddles(iwf_plan* p) {
 }
 
 iwf_status check_apply_error(iwf_plan* p, cudaStream_t stream) {
+  if (!p->d_apply_err) return IWF_OK;
   int err = 0;
   IWF_CUDA(cudaMemcpyAsync(&err, p->d_apply_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
   IWF_CUDA(cudaStreamSynchronize(stream));

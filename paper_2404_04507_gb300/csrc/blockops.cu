@@ -919,6 +919,15 @@ __global__ void random_kernel(typename Cplx<T>::type* X, long long count, unsign
   }
 }
 
+// flag = 1 when any of the count doubles is NaN or infinite
+__global__ void nonfinite_kernel(const double* x, long long count, int* flag) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 __global__ void mask_kernel(int nprob, int* mask, int off, int b, int value, const int* src) {
   const int prob = blockIdx.x;
   const int j = threadIdx.x;
@@ -1086,6 +1095,14 @@ iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cu
   const long long count = N * b;
   random_kernel<T><<<grid_for(count, 256), 256, 0, s>>>(
       reinterpret_cast<typename Cplx<T>::type*>(X), count, seed);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+iwf_status any_nonfinite(const double* x, long long count, int* flag, cudaStream_t s) {
+  IWF_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  nonfinite_kernel<<<grid_for(count, 256), 256, 0, s>>>(x, count, flag);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;

@@ -81,6 +81,8 @@ template <typename Tin, typename Tout>
 iwf_status convert_block(const void* in, void* out, long long count, cudaStream_t s);
 template <typename T>
 iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cudaStream_t s);
+// *flag = 1 (device int) when any of count doubles at x is NaN or infinite, else 0.
+iwf_status any_nonfinite(const double* x, long long count, int* flag, cudaStream_t s);
 // mask[p*kMaxSmall + off + j] = value (or src[p*kMaxBlock + j]) for j < b, every problem.
 iwf_status set_mask(const Batch& bt, int* mask, int off, int b, int value, const int* src,
                     cudaStream_t s);

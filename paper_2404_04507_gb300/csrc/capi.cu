@@ -355,6 +355,20 @@ iwf_status iwf_apply_noalloc(iwf_plan* p, int precision, const void* psi, void* 
   return apply_noalloc_impl(p, precision, psi, hpsi, nvec, (cudaStream_t)stream);
 }
 
+iwf_status iwf_plan_check(iwf_plan* p, void* stream) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_check: NULL plan");
+  DeviceGuard guard(p->device);
+  return check_apply_error(p, (cudaStream_t)stream);
+}
+
+iwf_status iwf_plan_set_wait_limit(iwf_plan* p, long long rounds) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_set_wait_limit: NULL plan");
+  p->wait_rounds = rounds < 0 ? -1 : rounds;
+  return IWF_OK;
+}
+
 iwf_status iwf_preconditioner(const iwf_plan* p, double* M, double* sigma) {
   if (!p) return fail(IWF_ERR_ARG, "iwf_preconditioner: NULL plan");
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_preconditioner: no potential set");

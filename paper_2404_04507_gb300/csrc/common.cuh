@@ -129,6 +129,7 @@ struct iwf_plan {
   float* d_lam32 = nullptr;
   int* d_err = nullptr;                   // device error word
   int* d_apply_err = nullptr;             // set by an apply kernel whose bounded wait ran out
+  long long wait_rounds = -1;             // main-wait bound of pipelined passes (-1: default)
   // potential
   int pot_kind = 0;                       // 0 unset, 1 tables, 2 grid
   double* d_tab64 = nullptr;

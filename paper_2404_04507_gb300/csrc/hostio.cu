@@ -104,8 +104,8 @@ iwf_status apply_host_impl(iwf_plan* p, int precision, const void* psi_host, voi
   }
   // the caller's stream continues after the last copy back; the call returns when it is done
   IWF_CUDA(cudaStreamWaitEvent(stream, ev[ev_out_free((nchunks - 1) & 1)], 0));
-  IWF_CUDA(cudaStreamSynchronize(stream));
-  return IWF_OK;
+  // synchronises `stream` and reports a pipelined pass that gave up waiting
+  return check_apply_error(p, stream);
 }
 
 }  // namespace iwf

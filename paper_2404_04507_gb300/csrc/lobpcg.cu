@@ -215,8 +215,9 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
     IWF_CUDA(cudaMemcpyAsync(h_resid.data(), sm.resid, sizeof(double) * np * kMaxBlock, cudaMemcpyDeviceToHost, st));
     IWF_CUDA(cudaMemcpyAsync(h_theta.data(), sm.theta, sizeof(double) * np * kMaxBlock, cudaMemcpyDeviceToHost, st));
     IWF_CUDA(cudaMemcpyAsync(h_status.data(), sm.status, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
-    IWF_CUDA(cudaStreamSynchronize(st));
-    return IWF_OK;
+    // the apply's device error word (a pipelined pass that gave up waiting), read at the
+    // same synchronisation point
+    return check_apply_error(p, st);
   };
   auto worst_of = [&](int q) {
     double w = 0;
@@ -242,9 +243,9 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
     bool any_pending = false, any_active = false;
     for (int q = 0; q < np; ++q) {
       if (!h_active[q]) continue;
-      if (h_status[q] != 0) return fail(IWF_ERR_BREAKDOWN, "Rayleigh-Ritz subspace lost rank");
       const double w = worst_of(q);
       if (!std::isfinite(w)) return fail(IWF_ERR_NONFINITE, "non-finite residual in the eigensolver");
+      if (h_status[q] != 0) return fail(IWF_ERR_BREAKDOWN, "Rayleigh-Ritz subspace lost rank");
       res.iters[q] = it;
       if (w <= tol) {
         if (pending[q]) { res.converged[q] = 1; h_active[q] = 0; pending[q] = 0; continue; }
@@ -394,8 +395,7 @@ iwf_status rayleigh_quotients(iwf_plan* p, const ApplyBatch* ab, Small& sm, Aren
   IWF_CUDA(cudaGetLastError());
   count_launch();
   IWF_CUDA(cudaMemcpyAsync(out, d_theta, sizeof(double) * np * nev, cudaMemcpyDeviceToHost, st));
-  IWF_CUDA(cudaStreamSynchronize(st));
-  return IWF_OK;
+  return check_apply_error(p, st);
 }
 
 // Shared driver: problems 0..np-1 with preconditioner parameters already on the device.
@@ -412,6 +412,17 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
   const auto t0 = std::chrono::steady_clock::now();
   double2* X;
   IWF_TRY(ar.get(&X, all));
+  if (X0) {
+    // a non-finite start block is an input error (it would otherwise surface later, or be
+    // masked by the orthonormalisation dropping its columns)
+    int* flag;
+    int h_flag = 0;
+    IWF_TRY(ar.get(&flag, 1));
+    IWF_TRY(any_nonfinite(reinterpret_cast<const double*>(X0), 2 * (long long)all, flag, st));
+    IWF_CUDA(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IWF_CUDA(cudaStreamSynchronize(st));
+    if (h_flag) return fail(IWF_ERR_NONFINITE, "iwf_eigensolve: non-finite start block X0");
+  }
   PhaseResult r1, r2;
   if (o->precision == IWF_PREC_C64) {
     float2* Xf;

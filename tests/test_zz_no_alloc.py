@@ -54,6 +54,31 @@ def test_noalloc_matches_apply_on_two_calls(iwf, dtype):
         assert err <= TOL[dtype] * want.abs().max().item(), (call, err)
 
 
+def test_noalloc_allocates_nothing_on_a_fresh_plan(iwf):
+    # the kernels are loaded first through another plan of the same geometry, so that lazy
+    # module loading does not count; then a fresh plan's first call is the allocation-free one
+    pb = W.config_moire(eps=5.0)
+    warm = iwf.Plan(pb.P, pb.K, pb.L)
+    warm.set_potential(pb.modes, pb.coef)
+    for dtype in (torch.complex128, torch.complex64):
+        x = torch.from_numpy(np.ascontiguousarray(W.random_block(warm.N, 2, seed=3).T)).to(dtype).cuda()
+        _noalloc(warm, x, torch.empty_like(x))
+    plan = iwf.Plan(pb.P, pb.K, pb.L)
+    plan.set_potential(pb.modes, pb.coef)
+    x = torch.from_numpy(np.ascontiguousarray(W.random_block(plan.N, 5, seed=9).T)).cuda()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    _noalloc(plan, x, y)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    # iwf_apply would size a workspace of a chunk of vectors (tens of MiB) on this plan
+    assert free0 - free1 < (2 << 20), (free0, free1)
+    want = plan.apply(x)
+    torch.cuda.synchronize()
+    assert (y - want).abs().max().item() <= 1e-12 * want.abs().max().item()
+
+
 def test_noalloc_small_plan_and_empty_block(iwf):
     pb = W.config_1d()
     plan = iwf.Plan(pb.P, pb.K, pb.L)
