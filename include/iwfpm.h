@@ -40,7 +40,7 @@ typedef enum {
 
 enum { IWF_METHOD_IWFPM = 0, IWF_METHOD_PM = 1 };
 enum { IWF_SHIFT_EXACT = 0, IWF_SHIFT_ROUND = 1 };
-enum { IWF_PREC_F64 = 0, IWF_PREC_C64 = 1, IWF_PREC_F64_EXACT = 2 };
+enum { IWF_PREC_F64 = 0, IWF_PREC_C64 = 1, IWF_PREC_F64_EXACT = 2, IWF_PREC_F64_DF = 3 };
 
 typedef struct iwf_plan iwf_plan; /* opaque, library-owned */
 
@@ -139,10 +139,14 @@ typedef struct {
   double tol;       /* stop when |H~x_i - lambda_i x_i|_2 <= tol for i < nev, |x_i|_2 = 1
                        (0: 1e-10)                                                           */
   int precision;    /* IWF_PREC_F64: every phase in complex double; the tall-skinny Gram
-                       products and block updates run in double-float arithmetic on the FP32
-                       pipes (products exact by fma, sums by TwoSum: about 48 significant
-                       bits). IWF_PREC_F64_EXACT: the same with FP64 arithmetic in those
-                       contractions (slower on this GPU, whose FP64 rate is 1/62 of FP32).
+                       products and block updates run on the tensor cores (tcgen05) by the
+                       Ozaki scheme: each FP64 value as seven 7-bit bf16 slices under a
+                       shared power-of-two scale, exact fp32 sums per slice level, about 49
+                       significant bits relative to the scales (iwf_gram).
+                       IWF_PREC_F64_DF: the same contractions in double-float arithmetic on the
+                       FP32 pipes (products exact by fma, sums by TwoSum: about 48 bits).
+                       IWF_PREC_F64_EXACT: FP64 arithmetic in those contractions (slow on this
+                       GPU, whose FP64 rate is 1/62 of FP32).
                        IWF_PREC_C64: a first phase with complex-float blocks and apply (FP64
                        small problems) until the residuals reach c64_tol or stall, then the
                        IWF_PREC_F64 phase to tol. Small problems are always FP64.          */
@@ -448,6 +452,35 @@ iwf_status iwf_plan_check(iwf_plan* plan, void* stream);
  * still lets them land before it exits.
  */
 iwf_status iwf_plan_set_wait_limit(iwf_plan* plan, long long rounds);
+
+/*
+ * The tall-skinny contractions of the eigensolver's Rayleigh-Ritz step (Sec. 4.1, Alg. 2 in
+ * block form: the Gram matrices S^H S and S^H H S and the updates X <- S C), exposed for
+ * direct use, testing and measurement. Engines:
+ *   IWF_CONTRACT_TENSOR  tcgen05 tensor cores, Ozaki scheme I: every FP64 value becomes the
+ *                        integer round(v 2^(48-E)) under a power-of-two scale 2^E shared by
+ *                        its group (a column for iwf_gram, a row of S and a column of C for
+ *                        iwf_block_update), written as seven balanced 7-bit digits stored as
+ *                        bf16; digit pairs of one level are summed exactly in fp32 tensor
+ *                        memory (levels 2..6; 7..9 share one accumulator; pairs above 9 are
+ *                        dropped). Error about 2^-49 of the product of the two scales per
+ *                        term, random in sign.
+ *   IWF_CONTRACT_DF      double-float arithmetic on the FP32 pipes (about 48 bits).
+ *   IWF_CONTRACT_F64     FP64 arithmetic.
+ * Matrices: A (nrows x ma), B (nrows x mb), S (nrows x m) and Y (nrows x q) are device,
+ * complex double, column-major with leading dimension nrows; G (ma x mb) and C (m x q) are
+ * device, complex double, row-major. ma, mb, m <= 72, q <= 24, nrows >= 1.
+ * Each call allocates and frees its scratch (a few MB) and synchronises `stream`.
+ * Errors: IWF_ERR_ARG (shape, NULL), IWF_ERR_ALLOC, IWF_ERR_CUDA, IWF_ERR_TIMEOUT (a bounded
+ * wait of the tensor-core pipeline ran out).
+ */
+enum { IWF_CONTRACT_TENSOR = 0, IWF_CONTRACT_DF = 1, IWF_CONTRACT_F64 = 2 };
+/* G = A^H B. */
+iwf_status iwf_gram(int engine, long long nrows, const void* A, int ma, const void* B, int mb,
+                    void* G, int device, void* stream);
+/* Y = S C, or Y = Y - S C when subtract != 0 (Y must not overlap S). */
+iwf_status iwf_block_update(int engine, long long nrows, const void* S, int m, const void* C,
+                            int q, void* Y, int subtract, int device, void* stream);
 
 #ifdef __cplusplus
 }

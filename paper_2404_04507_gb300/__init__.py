@@ -10,7 +10,7 @@ import ctypes as C
 
 import numpy as np
 
-__all__ = ["Plan"]
+__all__ = ["Plan", "gram", "block_update"]
 
 
 def _torch():
@@ -19,8 +19,10 @@ def _torch():
 
 
 def _solve_precision(c, precision):
-    """Solver precision names: "f64", "c64" (complex-float first phase) or "f64_exact"."""
-    table = {"f64": c.IWF_PREC_F64, "c64": c.IWF_PREC_C64, "f64_exact": c.IWF_PREC_F64_EXACT}
+    """Solver precision names: "f64" (tensor-core contractions), "c64" (complex-float first
+    phase), "f64_df" (double-float contractions) or "f64_exact" (FP64 contractions)."""
+    table = {"f64": c.IWF_PREC_F64, "c64": c.IWF_PREC_C64, "f64_exact": c.IWF_PREC_F64_EXACT,
+             "f64_df": c.IWF_PREC_F64_DF}
     if precision not in table:
         raise ValueError(f"precision must be one of {sorted(table)}")
     return table[precision]
@@ -369,6 +371,58 @@ class Plan:
             c.check(st, "iwf_batch_eigensolve")
         out = {f: getattr(info, f) for f, _ in c.iwf_solve_info._fields_}
         return evals, evecs, resid, iters, out
+
+
+_ENGINES = {"tensor": 0, "df": 1, "f64": 2}
+
+
+def _contract_args(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def gram(A, B, engine="tensor", stream=None):
+    """iwf_gram: G = A^H B for blocks given as (columns, nrows) complex128 CUDA tensors (each
+    row of the tensor is one column of the matrix). Returns G (ma, mb) on the device."""
+    from . import capi
+    torch = _torch()
+    _contract_args(A, "A"); _contract_args(B, "B")
+    ma, nrows = A.shape
+    mb = B.shape[0]
+    if B.shape[1] != nrows:
+        raise ValueError("A and B need the same number of rows")
+    G = torch.empty((ma, mb), dtype=torch.complex128, device=A.device)
+    capi.check(capi.iwf_gram(_ENGINES[engine], int(nrows), C.c_void_p(A.data_ptr()), int(ma),
+                             C.c_void_p(B.data_ptr()), int(mb), C.c_void_p(G.data_ptr()),
+                             A.device.index or 0, Plan._stream(stream)), "iwf_gram")
+    return G
+
+
+def block_update(S, Cm, Y=None, subtract=False, engine="tensor", stream=None):
+    """iwf_block_update: Y = S C (or Y -= S C) with S (m, nrows) and Y (q, nrows) given as
+    column blocks and C an (m, q) complex128 CUDA tensor (row-major). Returns Y."""
+    from . import capi
+    torch = _torch()
+    _contract_args(S, "S"); _contract_args(Cm, "C")
+    m, nrows = S.shape
+    q = Cm.shape[1]
+    if Cm.shape[0] != m:
+        raise ValueError("C must have one row per column of S")
+    if Y is None:
+        if subtract:
+            raise ValueError("subtract needs Y")
+        Y = torch.empty((q, nrows), dtype=torch.complex128, device=S.device)
+    _contract_args(Y, "Y")
+    capi.check(capi.iwf_block_update(_ENGINES[engine], int(nrows), C.c_void_p(S.data_ptr()),
+                                     int(m), C.c_void_p(Cm.data_ptr()), int(q),
+                                     C.c_void_p(Y.data_ptr()), int(bool(subtract)),
+                                     S.device.index or 0, Plan._stream(stream)),
+               "iwf_block_update")
+    return Y
 
 
 def kernel_launches() -> int:

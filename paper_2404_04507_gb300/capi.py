@@ -18,7 +18,8 @@ STATUS = {0: "IWF_OK", -1: "IWF_ERR_ARG", -2: "IWF_ERR_SINGULAR_PI", -3: "IWF_ER
           -10: "IWF_ERR_UNSUPPORTED"}
 IWF_METHOD_IWFPM, IWF_METHOD_PM = 0, 1
 IWF_SHIFT_EXACT, IWF_SHIFT_ROUND = 0, 1
-IWF_PREC_F64, IWF_PREC_C64, IWF_PREC_F64_EXACT = 0, 1, 2
+IWF_PREC_F64, IWF_PREC_C64, IWF_PREC_F64_EXACT, IWF_PREC_F64_DF = 0, 1, 2, 3
+IWF_CONTRACT_TENSOR, IWF_CONTRACT_DF, IWF_CONTRACT_F64 = 0, 1, 2
 IWF_PATH_AUTO, IWF_PATH_TILED, IWF_PATH_PENCIL = 0, 1, 2
 
 
@@ -99,6 +100,8 @@ _PROTOS = {
     "iwf_ws_embed": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
     "iwf_ws_phase": (_i, [_vp, _i, _i, C.POINTER(C.c_double), _i, _vp, _vp]),
     "iwf_plan_check": (_i, [_vp, _vp]),
+    "iwf_gram": (_i, [_i, _ll, _vp, _i, _vp, _i, _vp, _i, _vp]),
+    "iwf_block_update": (_i, [_i, _ll, _vp, _i, _vp, _i, _vp, _i, _i, _vp]),
     "iwf_plan_set_wait_limit": (_i, [_vp, _ll]),
 }
 for _name, (_res, _args) in _PROTOS.items():

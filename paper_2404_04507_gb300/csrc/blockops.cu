@@ -950,11 +950,13 @@ iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long lo
   const int ma = A.nb * A.b, mb = B.nb * B.b;
   if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram: too many columns");
   if (herm && ma != mb) return fail(IWF_ERR_ARG, "gram: a Hermitian product must be square");
+  if (sizeof(T) == 8 && bt.engine == kEngineTensor)
+    return gram_tc(bt, A, B, N, out, reinterpret_cast<double*>(partial), slots_per_prob, bt.err, s);
   int g = grid_for(N, kGramRows);
   if (g > slots_per_prob) g = slots_per_prob;
   const int U = (ma + kGramTx - 1) / kGramTx, V = (mb + kGramTx - 1) / kGramTx;
   const dim3 grid(g, bt.nprob);
-  const bool df = sizeof(T) == 8 && !bt.exact64;
+  const bool df = sizeof(T) == 8 && bt.engine == kEngineDF;
   switch (U * 4 + V + (herm ? 100 : 0)) {
 #define IWF_GRAM(U_, V_, H_) \
     case U_ * 4 + V_ + (H_ ? 100 : 0): \
@@ -986,6 +988,9 @@ iwf_status block_update(const Batch& bt, const BlockList& S, long long N, const 
   const int m = S.nb * S.b;
   if (m > kMaxSmall || q > kMaxBlock || q < 1) return fail(IWF_ERR_ARG, "block_update: shape");
   if (cstride < m * q) return fail(IWF_ERR_ARG, "block_update: coefficient stride too small");
+  if (sizeof(T) == 8 && bt.engine == kEngineTensor)
+    return update_tc(bt, S, N, C1, C2, cstride, q, reinterpret_cast<double2*>(out1),
+                     reinterpret_cast<double2*>(out2), subtract, bt.err, s);
   int g0 = grid_for(N, kUpdRows);
   if (bt.nprob > 1) g0 = std::max(1, std::min(g0, (8 * 152 + bt.nprob - 1) / bt.nprob));
   const dim3 g(g0, bt.nprob);
@@ -1000,7 +1005,7 @@ iwf_status block_update(const Batch& bt, const BlockList& S, long long N, const 
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     attr[subtract] = true;
   }
-  if (sizeof(T) == 8 && !bt.exact64) {
+  if (sizeof(T) == 8 && bt.engine == kEngineDF) {
     static bool attr_df[2] = {false, false};
     if (!attr_df[subtract]) {
       if (subtract)

@@ -39,14 +39,17 @@ __device__ __forceinline__ const typename Cplx<T>::type* col_ptr(const BlockList
 // Small per-problem matrices sit at fixed capacities: G kMaxSmall^2, C kMaxSmall*kMaxBlock,
 // T kMaxBlock^2, theta/resid kMaxBlock, masks kMaxSmall. active (may be null): problems
 // with active[p] == 0 are skipped by every kernel.
+// Engines of the complex-double Gram products and block updates.
+enum { kEngineTensor = 0,   // tcgen05 tensor cores, Ozaki scheme I (bf16 slices, ozaki.cu)
+       kEngineDF = 1,       // double-float arithmetic on the FP32 pipes (about 48 bits)
+       kEngineF64 = 2 };    // FP64 arithmetic
 struct Batch {
   int nprob;
   long long pstride;
   const int* active;
-  // complex-double blocks: 0 computes Gram products and block updates in double-float
-  // arithmetic on the FP32 pipes (products exact by fma, sums by TwoSum, about 48 bits),
-  // 1 in FP64 arithmetic
-  int exact64 = 0;
+  int engine = kEngineTensor;
+  int* exps = nullptr;      // tensor engine: column scales, nprob x 2 kMaxSmall ints
+  int* err = nullptr;       // tensor engine: device error word for a bounded wait that ran out
 };
 constexpr int kCapG = kMaxSmall * kMaxSmall;
 constexpr int kCapC = kMaxSmall * kMaxBlock;
@@ -81,6 +84,13 @@ template <typename Tin, typename Tout>
 iwf_status convert_block(const void* in, void* out, long long count, cudaStream_t s);
 template <typename T>
 iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cudaStream_t s);
+// Tensor-core (Ozaki scheme I) versions of gram<double> and block_update<double> (ozaki.cu);
+// partial holds nprob x slots_cap x 2 kCapG doubles.
+iwf_status gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, long long N,
+                   double2* out, double* partial, int slots_cap, int* err, cudaStream_t s);
+iwf_status update_tc(const Batch& bt, const BlockList& S, long long N, const double2* C1,
+                     const double2* C2, int cstride, int q, double2* out1, double2* out2,
+                     bool subtract, int* err, cudaStream_t s);
 // *flag = 1 (device int) when any of count doubles at x is NaN or infinite, else 0.
 iwf_status any_nonfinite(const double* x, long long count, int* flag, cudaStream_t s);
 // mask[p*kMaxSmall + off + j] = value (or src[p*kMaxBlock + j]) for j < b, every problem.

@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include "blockops.cuh"
 #include "common.cuh"
 
 namespace iwf {
@@ -384,6 +385,89 @@ iwf_status iwf_preconditioner(const iwf_plan* p, double* M, double* sigma) {
     }
   }
   return IWF_OK;
+}
+
+}  // extern "C"
+
+// ---- the eigensolver's contractions as entry points (iwf_gram, iwf_block_update) ----------
+namespace {
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() { for (void* p : ptrs) cudaFree(p); }
+  iwf_status get(void** out, size_t bytes) {
+    if (cudaMalloc(out, bytes) != cudaSuccess) return iwf::fail(IWF_ERR_ALLOC, "contraction scratch");
+    ptrs.push_back(*out);
+    return IWF_OK;
+  }
+};
+
+iwf_status contract_batch(int engine, Scratch& sc, iwf::Batch* bt) {
+  if (engine != IWF_CONTRACT_TENSOR && engine != IWF_CONTRACT_DF && engine != IWF_CONTRACT_F64)
+    return iwf::fail(IWF_ERR_ARG, "unknown contraction engine");
+  bt->nprob = 1;
+  bt->pstride = 0;
+  bt->active = nullptr;
+  bt->engine = engine == IWF_CONTRACT_TENSOR ? iwf::kEngineTensor
+               : engine == IWF_CONTRACT_DF   ? iwf::kEngineDF
+                                             : iwf::kEngineF64;
+  void *e = nullptr, *w = nullptr;
+  IWF_TRY(sc.get(&e, sizeof(int) * 2 * iwf::kMaxSmall));
+  IWF_TRY(sc.get(&w, sizeof(int)));
+  IWF_CUDA(cudaMemset(w, 0, sizeof(int)));
+  bt->exps = static_cast<int*>(e);
+  bt->err = static_cast<int*>(w);
+  return IWF_OK;
+}
+
+iwf_status contract_finish(const iwf::Batch& bt, cudaStream_t st) {
+  int h = 0;
+  IWF_CUDA(cudaMemcpyAsync(&h, bt.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IWF_CUDA(cudaStreamSynchronize(st));
+  if (h) return iwf::fail(IWF_ERR_TIMEOUT, "tensor-core contraction: a bounded wait ran out");
+  return IWF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+iwf_status iwf_gram(int engine, long long nrows, const void* A, int ma, const void* B, int mb,
+                    void* G, int device, void* stream) {
+  clear_error();
+  if (!A || !B || !G || nrows < 1 || ma < 1 || mb < 1 || ma > kMaxSmall || mb > kMaxSmall)
+    return fail(IWF_ERR_ARG, "iwf_gram: bad arguments");
+  DeviceGuard guard(device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc;
+  Batch bt;
+  IWF_TRY(contract_batch(engine, sc, &bt));
+  const int slots = 608;
+  void *part = nullptr, *out = nullptr;
+  IWF_TRY(sc.get(&part, sizeof(double2) * (size_t)slots * kCapG));
+  IWF_TRY(sc.get(&out, sizeof(double2) * kCapG));
+  BlockList LA{}, LB{};
+  LA.p[0] = A; LA.nb = 1; LA.b = ma;
+  LB.p[0] = B; LB.nb = 1; LB.b = mb;
+  IWF_TRY(gram<double>(bt, LA, LB, nrows, static_cast<double2*>(out),
+                       static_cast<double2*>(part), slots, st, false));
+  IWF_CUDA(cudaMemcpyAsync(G, out, sizeof(double2) * (size_t)ma * mb, cudaMemcpyDeviceToDevice, st));
+  return contract_finish(bt, st);
+}
+
+iwf_status iwf_block_update(int engine, long long nrows, const void* S, int m, const void* C,
+                            int q, void* Y, int subtract, int device, void* stream) {
+  clear_error();
+  if (!S || !C || !Y || nrows < 1 || m < 1 || m > kMaxSmall || q < 1 || q > kMaxBlock)
+    return fail(IWF_ERR_ARG, "iwf_block_update: bad arguments");
+  DeviceGuard guard(device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc;
+  Batch bt;
+  IWF_TRY(contract_batch(engine, sc, &bt));
+  BlockList LS{};
+  LS.p[0] = S; LS.nb = 1; LS.b = m;
+  IWF_TRY(block_update<double>(bt, LS, nrows, static_cast<const double2*>(C), nullptr, m * q, q,
+                               Y, nullptr, subtract != 0, st));
+  return contract_finish(bt, st);
 }
 
 }  // extern "C"

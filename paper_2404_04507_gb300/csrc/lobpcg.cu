@@ -67,6 +67,7 @@ struct Small {
   double2 *G, *Cx, *Cp, *T, *partial;
   double *theta, *resid, *rpartial;
   int *mask, *maskw, *maskp, *status, *active;
+  int* exps;                   // column scales of the tensor-core Gram products
   double *shift, *off2;        // preconditioner parameters per problem
 };
 
@@ -86,6 +87,7 @@ iwf_status alloc_small(Arena& ar, Small& s, int nprob) {
   IWF_TRY(ar.get(&s.active, (size_t)nprob));
   IWF_TRY(ar.get(&s.shift, (size_t)nprob));
   IWF_TRY(ar.get(&s.off2, (size_t)nprob));
+  IWF_TRY(ar.get(&s.exps, (size_t)nprob * 2 * kMaxSmall));
   IWF_TRY(ar.get(&s.partial, (size_t)nprob * s.slots * kCapG));
   IWF_TRY(ar.get(&s.rpartial, (size_t)nprob * s.slots * kMaxBlock));
   return IWF_OK;
@@ -126,7 +128,7 @@ struct Graph {
 template <typename T>
 iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxit, double tol,
                      int stall, void* Xio, Small& sm, Arena& ar, cudaStream_t st,
-                     PhaseResult& res, bool exact64) {
+                     PhaseResult& res, int engine) {
   using V2 = typename Cplx<T>::type;
   const int np = sm.nprob;
   const long long N = p->g.N;
@@ -138,7 +140,7 @@ iwf_status run_phase(iwf_plan* p, const ApplyBatch* ab, int b, int nev, int maxi
   IWF_TRY(ar.get(&HX2, all)); IWF_TRY(ar.get(&P2, all)); IWF_TRY(ar.get(&HP2, all));
   IWF_TRY(ar.get(&W2, all));
   X = reinterpret_cast<V2*>(Xio);
-  Batch bt{np, (long long)blk, sm.active, exact64 ? 1 : 0};
+  Batch bt{np, (long long)blk, sm.active, engine, sm.exps, p->d_apply_err};
   const int prec = prec_of<T>();
   std::vector<double> h_resid((size_t)np * kMaxBlock), h_theta((size_t)np * kMaxBlock);
   std::vector<int> h_status(np), h_active(np, 1);
@@ -430,15 +432,17 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
     if (X0) IWF_TRY((convert_block<double, float>(X0, Xf, 2 * (long long)all, st)));
     else IWF_TRY(random_block<float>(Xf, N, b * np, o->seed, st));
     const double tol1 = std::max(tol, o->c64_tol > 0 ? o->c64_tol : 1e-5);
-    IWF_TRY(run_phase<float>(p, ab, b, nev, maxit, tol1, 10, Xf, sm, ar, st, r1, false));
+    IWF_TRY(run_phase<float>(p, ab, b, nev, maxit, tol1, 10, Xf, sm, ar, st, r1, kEngineTensor));
     IWF_TRY((convert_block<float, double>(Xf, X, 2 * (long long)all, st)));
   } else {
     if (X0) IWF_CUDA(cudaMemcpyAsync(X, X0, sizeof(double2) * all, cudaMemcpyDeviceToDevice, st));
     else IWF_TRY(random_block<double>(X, N, b * np, o->seed, st));
   }
   const int left = std::max(1, maxit - r1.rounds);
-  IWF_TRY(run_phase<double>(p, ab, b, nev, left, tol, 0, X, sm, ar, st, r2,
-                            o->precision == IWF_PREC_F64_EXACT));
+  const int engine = o->precision == IWF_PREC_F64_EXACT ? kEngineF64
+                     : o->precision == IWF_PREC_F64_DF  ? kEngineDF
+                                                        : kEngineTensor;
+  IWF_TRY(run_phase<double>(p, ab, b, nev, left, tol, 0, X, sm, ar, st, r2, engine));
   std::vector<double> rq((size_t)np * nev);
   long long rq_applies = 0;
   IWF_TRY(rayleigh_quotients(p, ab, sm, ar, X, b, nev, rq.data(), &rq_applies, st));
@@ -481,7 +485,7 @@ iwf_status check_opts(const iwf_plan* p, const iwf_solve_opts* o) {
     return fail(IWF_ERR_ARG, "iwf_eigensolve: need 1 <= nev <= block <= 24");
   if ((long long)3 * b > p->g.N) return fail(IWF_ERR_ARG, "iwf_eigensolve: window too small for the block");
   if (o->precision != IWF_PREC_F64 && o->precision != IWF_PREC_C64 &&
-      o->precision != IWF_PREC_F64_EXACT)
+      o->precision != IWF_PREC_F64_EXACT && o->precision != IWF_PREC_F64_DF)
     return fail(IWF_ERR_ARG, "iwf_eigensolve: unknown precision");
   return IWF_OK;
 }

@@ -1,0 +1,831 @@
+// FP64-accurate tall-skinny contractions of the eigensolver on the tcgen05 tensor cores
+// (Ozaki scheme I with fixed-point bf16 slices):
+//   Gram   G = A^H B      (A: N x ma, B: N x mb complex double, contraction over N rows)
+//   update Y = S C        (S: N x m, C: m x q complex double, contraction over m)
+// These are the dense contractions of the Rayleigh-Ritz step of LOBPCG (Sec. 4.1, Alg. 2
+// in block form).
+//
+// Slicing. Every value v of a group that shares one scale 2^E (a column of a Gram operand,
+// a row of an update operand; |v| < 2^E) becomes the 49-bit integer I = round(v 2^(48-E)),
+// written in balanced base-128 digits I = sum_k d_k 2^(49-7k), k = 1..7, |d_k| <= 64. Digit k
+// is stored as the bf16 value d_k 2^(-7(k-1)) (exact: at most 7 significant bits), so
+// v = 2^(E-6) sum_k D_k. A product of two values expands into digit pairs (k, l); pairs of one
+// level k + l are integer multiples of one unit 2^(-7(k+l-2)). The tensor core multiplies
+// bf16 pairs exactly and adds them in fp32; with |d| <= 64 a level's sum over a bounded
+// number of rows stays below 2^24 units, so levels 2..6 each keep an exact fp32 accumulator
+// in tensor memory, and levels 7..9 share one (their rounding sits below 2^-52 of the
+// result). Pairs with k + l >= 10 are dropped (below 2^-50 of the scales' product, with
+// random sign: the digits are balanced). Exact level sums are moved into double-float
+// registers (Gram: every few hundred rows) or assembled into FP64 (update).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "blockops.cuh"
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace iwf {
+
+namespace {
+
+constexpr int kDig = 7;                 // digits per value
+constexpr int kMaxLvl = 9;              // pairs k + l <= 9
+constexpr int kNumAcc = 6;              // levels 2..6 exact, 7..9 shared
+constexpr long long kTcSpin = 1LL << 22;  // bounded mbarrier waits (try_wait rounds)
+constexpr int kErrTimeout = 1;
+
+__device__ __forceinline__ int acc_of_level(int lvl) { return lvl <= 6 ? lvl - 2 : 5; }
+
+// Balanced base-128 digits of round(v 2^(48-E)), where the group's largest biased exponent is
+// maxb (E = maxb - 1022). Zeros, denormals and values far below 2^E give zero digits.
+__device__ __forceinline__ void digits7(double v, int maxb, int (&d)[kDig]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  int s = 5 + maxb - e;
+  s = s < 5 ? 5 : s;
+  long long I = 0;
+  if (e != 0 && s < 64) {
+    const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    I = (long long)((M + (1ull << (s - 1))) >> s);
+    if (bits >> 63) I = -I;
+  }
+  long long r = I;
+  const int d1 = (int)((r + (1LL << 41)) >> 42); r -= (long long)d1 << 42;
+  const int d2 = (int)((r + (1LL << 34)) >> 35); r -= (long long)d2 << 35;
+  const int d3 = (int)((r + (1LL << 27)) >> 28); r -= (long long)d3 << 28;
+  int q = (int)r;
+  const int d4 = (q + (1 << 20)) >> 21; q -= d4 << 21;
+  const int d5 = (q + (1 << 13)) >> 14; q -= d5 << 14;
+  const int d6 = (q + (1 << 6)) >> 7; q -= d6 << 7;
+  d[0] = d1; d[1] = d2; d[2] = d3; d[3] = d4; d[4] = d5; d[5] = d6; d[6] = q;
+}
+
+// Bits of the float d * 2^(-7k) (|d| <= 64: exact, low 16 bits zero, so its top half is bf16).
+__device__ __forceinline__ uint32_t digit_bits(int d, int k) {
+  const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) *
+                  __int_as_float((127 - 7 * k) << 23);
+  return __float_as_uint(f);
+}
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, 0x7632);
+}
+
+// Digits of 8 consecutive values of one group, written as the 16-byte K-row of one tile row
+// in each of the 7 digit tiles (tile k at base + k * tile_stride).
+__device__ __forceinline__ void store_digits8(const double (&v)[8], int maxb, unsigned char* base,
+                                              uint32_t tile_stride, uint32_t off) {
+  uint32_t w[kDig][4];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    int a[kDig], b[kDig];
+    digits7(v[j], maxb, a);
+    digits7(v[j + 1], maxb, b);
+#pragma unroll
+    for (int k = 0; k < kDig; ++k) w[k][j / 2] = pack2(digit_bits(a[k], k), digit_bits(b[k], k));
+  }
+#pragma unroll
+  for (int k = 0; k < kDig; ++k)
+    *reinterpret_cast<uint4*>(base + (size_t)k * tile_stride + off) =
+        make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
+}
+
+// Offset of (tile row rho, K half h) in a no-swizzle K-major K16 tile.
+__device__ __forceinline__ uint32_t tile_off(int rho, int h) {
+  return (uint32_t)((rho >> 3) * tc::kSBO + h * tc::kLBO + (rho & 7) * 16);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
+  for (long long r = 0; r < kTcSpin; ++r)
+    if (tc::bar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------------------
+// Column scales: exps[c] = largest biased FP64 exponent over the re and im parts of column c
+// (2047 when the column holds an Inf or NaN, 0 for a zero column). exps must start at 0.
+__global__ void colexp_kernel(Batch bt, BlockList A, long long N, int* exps) {
+  const int prob = blockIdx.z, c = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const double2* col = reinterpret_cast<const double2*>(A.p[c / A.b]) +
+                       (size_t)prob * bt.pstride + (size_t)(c % A.b) * N;
+  unsigned int m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = col[i];
+    const unsigned int hx = (unsigned int)(__double_as_longlong(v.x) >> 32);
+    const unsigned int hy = (unsigned int)(__double_as_longlong(v.y) >> 32);
+    m = max(m, max((hx >> 20) & 0x7FFu, (hy >> 20) & 0x7FFu));
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(exps + (size_t)prob * 2 * kMaxSmall + c, (int)m);
+}
+
+// ---------------------------------------------------------------------------------------
+// Gram kernel. Roles: warps 0..7 slice 16-row stages of A and B into the digit tiles; warp 8
+// issues the MMAs; warps 9..16 move the level accumulators into double-float running sums
+// every CHUNK rows and write the CTA's partial at the end.
+//   FULL (2 ma <= 128, 2 mb <= 80): D = [Ar; Ai]^T [Br, Bi] in one accumulator set
+//     (M = 2ma, N = 2mb); the reduction forms re = ArBr + AiBi, im = ArBi - AiBr.
+//   SPLIT (ma <= 128, mb <= 80): blockIdx.z = 0 accumulates ArBr + AiBi, z = 1 ArBi - AiBr.
+constexpr int kProdWarps = 8, kEpiWarps = 8;
+constexpr int kGramThreads = (kProdWarps + 1 + kEpiWarps) * 32;
+constexpr int kTileA = 128 * tc::kTileRowBytes;     // 4 KB: M = 128 rows x K16
+
+template <bool SPLIT, int NMMA>
+struct GramCfg {
+  static constexpr int kTileB = NMMA * tc::kTileRowBytes;
+  static constexpr int kATiles = SPLIT ? 2 : 1;    // Ar, Ai (SPLIT) or [Ar; Ai]
+  static constexpr int kBTiles = SPLIT ? 2 : 1;
+  static constexpr int kStageBytes = kDig * (kATiles * kTileA + kBTiles * kTileB);
+  static constexpr int kStages = SPLIT ? 2 : 4;
+  static constexpr int kChunkRows = SPLIT ? 256 : 512;   // level sums stay below 2^24
+  static constexpr int kSmem = kStages * kStageBytes + 1024;
+};
+
+template <bool SPLIT, int NMMA>
+__global__ void __launch_bounds__(kGramThreads, 1)
+gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
+               long long rows_per_slot, double* partial, int* err) {
+  using Cfg = GramCfg<SPLIT, NMMA>;
+  constexpr int S = Cfg::kStages;
+  const int prob = blockIdx.y, slot = blockIdx.x, z = SPLIT ? blockIdx.z : 0;
+  if (bt.active && !bt.active[prob]) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full_bar[S], empty_bar[S], accf_bar, acce_bar;
+  __shared__ __align__(8) unsigned long long done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t poff = (size_t)prob * bt.pstride;
+  const int* expA = bt.exps + (size_t)prob * 2 * kMaxSmall;
+  const int* expB = expA + kMaxSmall;
+  const long long r_begin = (long long)slot * rows_per_slot;
+  const long long r_end = min(N, r_begin + rows_per_slot);
+  const long long nrows = r_end > r_begin ? r_end - r_begin : 0;
+  const int nstages = (int)((nrows + 15) / 16);
+  constexpr int kStagesPerChunk = Cfg::kChunkRows / 16;
+  const int nchunks = (nstages + kStagesPerChunk - 1) / kStagesPerChunk;
+
+  // zero every stage (padding rows of the tiles stay zero), barriers, tensor memory
+  for (int i = threadIdx.x; i < S * Cfg::kStageBytes / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::bar_init(tc::smem_u32(&full_bar[s]), kProdWarps * 32);
+      tc::bar_init(tc::smem_u32(&empty_bar[s]), 1);
+    }
+    tc::bar_init(tc::smem_u32(&accf_bar), 1);
+    tc::bar_init(tc::smem_u32(&acce_bar), kEpiWarps * 32);
+    tc::bar_init(tc::smem_u32(&done_bar), 1);
+    tc::bar_init_fence();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(&tmem_base), 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp < kProdWarps) {
+    // ---- producers: one item = (column, K half) of A or B, 8 rows x (re, im) ----
+    const int tid = threadIdx.x;
+    const int items = 2 * (ma + mb);
+    for (int j = 0; j < nstages; ++j) {
+      const int st = j % S;
+      if (!wait_bounded(tc::smem_u32(&empty_bar[st]), (uint32_t)(((j / S) & 1) ^ 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*abort_v) break;
+      unsigned char* stage = smem + (size_t)st * Cfg::kStageBytes;
+      unsigned char* tA = stage;                                        // [kATiles][kDig] tiles
+      unsigned char* tB = stage + kDig * Cfg::kATiles * kTileA;          // [kBTiles][kDig] tiles
+      const long long r0 = r_begin + 16LL * j;
+      for (int it = tid; it < items; it += kProdWarps * 32) {
+        const int h = it & 1, cc = it >> 1;
+        const bool isA = cc < ma;
+        const int c = isA ? cc : cc - ma;
+        const BlockList& L = isA ? A : B;
+        const double2* col = reinterpret_cast<const double2*>(L.p[c / L.b]) + poff +
+                             (size_t)(c % L.b) * N;
+        double re[8], im[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long r = r0 + 8 * h + u;
+          double2 v = make_double2(0.0, 0.0);
+          if (r < r_end) v = col[r];
+          re[u] = v.x; im[u] = v.y;
+        }
+        const int maxb = isA ? expA[c] : expB[c];
+        if (isA) {
+          if (SPLIT) {
+            store_digits8(re, maxb, tA, kTileA, tile_off(c, h));
+            store_digits8(im, maxb, tA + kDig * kTileA, kTileA, tile_off(c, h));
+          } else {
+            store_digits8(re, maxb, tA, kTileA, tile_off(c, h));
+            store_digits8(im, maxb, tA, kTileA, tile_off(c + ma, h));
+          }
+        } else {
+          if (SPLIT) {
+            store_digits8(re, maxb, tB, Cfg::kTileB, tile_off(c, h));
+            store_digits8(im, maxb, tB + kDig * Cfg::kTileB, Cfg::kTileB, tile_off(c, h));
+          } else {
+            store_digits8(re, maxb, tB, Cfg::kTileB, tile_off(c, h));
+            store_digits8(im, maxb, tB, Cfg::kTileB, tile_off(c + mb, h));
+          }
+        }
+      }
+      tc::fence_async_smem();
+      tc::bar_arrive(tc::smem_u32(&full_bar[st]));
+    }
+  } else if (warp == kProdWarps) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idn = tc::idesc_bf16(128, NMMA, false);
+      const uint32_t idneg = tc::idesc_bf16(128, NMMA, true);
+      bool started[kNumAcc];
+      for (int j = 0; j < nstages && !*abort_v; ++j) {
+        const int st = j % S;
+        const int chunk = j / kStagesPerChunk;
+        if (j % kStagesPerChunk == 0) {
+          if (chunk > 0 &&
+              !wait_bounded(tc::smem_u32(&acce_bar), (uint32_t)((chunk - 1) & 1))) {
+            atomicExch(&abort_flag, 1);
+            break;
+          }
+          for (int a = 0; a < kNumAcc; ++a) started[a] = false;
+        }
+        if (!wait_bounded(tc::smem_u32(&full_bar[st]), (uint32_t)((j / S) & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sbase = tc::smem_u32(smem + (size_t)st * Cfg::kStageBytes);
+        const uint32_t aBase = sbase, bBase = sbase + kDig * Cfg::kATiles * kTileA;
+        for (int k = 0; k < kDig; ++k) {
+          for (int l = 0; l < kDig; ++l) {
+            if (k + l + 2 > kMaxLvl) continue;
+            const int acc = acc_of_level(k + l + 2);
+            const uint32_t d = tmem + (uint32_t)(acc * NMMA);
+            if (!SPLIT) {
+              tc::mma_bf16(d, tc::sdesc(aBase + k * kTileA), tc::sdesc(bBase + l * Cfg::kTileB),
+                           idn, started[acc]);
+            } else {
+              const uint32_t ar = aBase + k * kTileA, ai = aBase + (kDig + k) * kTileA;
+              const uint32_t br = bBase + l * Cfg::kTileB, bi = bBase + (kDig + l) * Cfg::kTileB;
+              if (z == 0) {
+                tc::mma_bf16(d, tc::sdesc(ar), tc::sdesc(br), idn, started[acc]);
+                tc::mma_bf16(d, tc::sdesc(ai), tc::sdesc(bi), idn, true);
+              } else {
+                tc::mma_bf16(d, tc::sdesc(ar), tc::sdesc(bi), idn, started[acc]);
+                tc::mma_bf16(d, tc::sdesc(ai), tc::sdesc(br), idneg, true);
+              }
+            }
+            started[acc] = true;
+          }
+        }
+        tc::mma_commit(tc::smem_u32(&empty_bar[st]));
+        if (j % kStagesPerChunk == kStagesPerChunk - 1 || j == nstages - 1)
+          tc::mma_commit(tc::smem_u32(&accf_bar));
+      }
+      // every MMA issued has completed before the kernel releases tensor memory
+      tc::mma_commit(tc::smem_u32(&done_bar));
+      wait_bounded(tc::smem_u32(&done_bar), 0);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: level accumulators -> double-float running sums ----
+    const int e = warp - kProdWarps - 1;            // 0..7
+    const int q = warp & 3;                         // TMEM lane quarter of this warp
+    const int half = e >= 4 ? 1 : 0;
+    constexpr int G = NMMA / 8;                     // 8-column groups
+    constexpr int GH = (G + 1) / 2;
+    const int g0 = half ? GH : 0, g1 = half ? G : GH;
+    const int lane_row = 32 * q + lane;             // accumulator row
+    float hi[GH * 8], lo[GH * 8];
+#pragma unroll
+    for (int i = 0; i < GH * 8; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+    for (int c = 0; c < nchunks && !*abort_v; ++c) {
+      if (!wait_bounded(tc::smem_u32(&accf_bar), (uint32_t)(c & 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int gi = 0; gi < GH; ++gi) {
+        const int g = g0 + gi;
+        if (g < g1) {
+#pragma unroll
+          for (int a = 0; a < kNumAcc; ++a) {
+            float v[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * NMMA + 8 * g), v);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              float s, er;
+              two_sum(hi[gi * 8 + u], v[u], s, er);
+              hi[gi * 8 + u] = s;
+              lo[gi * 8 + u] += er;
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::bar_arrive(tc::smem_u32(&acce_bar));
+    }
+    // partial of this CTA: FULL rows 2ma x cols 2mb; SPLIT [z] rows ma x cols mb
+    const int Mrows = SPLIT ? ma : 2 * ma, Ncols = SPLIT ? mb : 2 * mb;
+    double* out = partial + (((size_t)prob * gridDim.x + slot) * (SPLIT ? 2 : 1) + z) *
+                                (size_t)(Mrows * Ncols);
+    if (lane_row < Mrows) {
+#pragma unroll
+      for (int gi = 0; gi < GH; ++gi) {
+        const int g = g0 + gi;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int col = 8 * g + u;
+          if (g < g1 && col < Ncols)
+            out[(size_t)lane_row * Ncols + col] = (double)hi[gi * 8 + u] + (double)lo[gi * 8 + u];
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (*abort_v && threadIdx.x == 0) atomicExch(err, kErrTimeout);
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// G[prob] (ma x mb, row-major, complex double at out + prob * kCapG) from the slot partials,
+// with the column scales 2^(Ea + Eb - 12), E = maxb - 1022.
+template <bool SPLIT>
+__global__ void gram_tc_reduce(Batch bt, const double* partial, int slots, int ma, int mb,
+                               double2* out) {
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ma * mb) return;
+  const int a = e / mb, b = e % mb;
+  const int* expA = bt.exps + (size_t)prob * 2 * kMaxSmall;
+  const int* expB = expA + kMaxSmall;
+  const int ea = expA[a], eb = expB[b];
+  double re = 0.0, im = 0.0;
+  if (!SPLIT) {
+    const int Nc = 2 * mb;
+    const size_t sz = (size_t)(2 * ma) * Nc;
+    const double* p = partial + (size_t)prob * slots * sz;
+    for (int s = 0; s < slots; ++s, p += sz) {
+      re += p[(size_t)a * Nc + b] + p[(size_t)(a + ma) * Nc + b + mb];
+      im += p[(size_t)a * Nc + b + mb] - p[(size_t)(a + ma) * Nc + b];
+    }
+  } else {
+    const size_t sz = (size_t)ma * mb;
+    const double* p = partial + (size_t)prob * slots * 2 * sz;
+    for (int s = 0; s < slots; ++s, p += 2 * sz) {
+      re += p[(size_t)a * mb + b];
+      im += p[sz + (size_t)a * mb + b];
+    }
+  }
+  double2 g;
+  if (ea >= 2047 || eb >= 2047) {
+    g = make_double2(nan(""), nan(""));
+  } else {
+    const double sc = ldexp(1.0, ea + eb - 2044 - 12);
+    g = make_double2(re * sc, im * sc);
+  }
+  out[(size_t)prob * kCapG + e] = g;
+}
+
+// ---------------------------------------------------------------------------------------
+// Update kernel: Y_o = S C_o (or Y_0 -= S C_0) for 128-row tiles of S. MMA M = 128 rows,
+// N = 2q (row 2j of B gives Re Y_j, row 2j+1 Im Y_j), K = 2m with the re and im parts of each
+// S column interleaved. Row scales of S come from a first pass over the tile (its data then
+// sits in L2 for the second pass that slices it); column scales of C are computed once per
+// CTA. One CTA per SM, persistent over tiles; blockIdx.x = 2 * slot + o for two outputs, so
+// that the two CTAs reading one tile run side by side. Roles: warps 0..7 slice (K16 slices of
+// 8 S columns into a 3-slot ring), warp 8 issues the MMAs, warps 9..12 assemble the FP64
+// outputs from the level accumulators with integer arithmetic.
+constexpr int kUpdProd = 8, kUpdEpi = 4;
+constexpr int kUpdThreads = (kUpdProd + 1 + kUpdEpi) * 32;
+constexpr int kUpdSlots = 3;
+constexpr int kRxRing = 2;                               // row-scale buffers in flight
+constexpr int kUpdSliceBytes = kDig * kTileA;            // 7 digit tiles of 128 rows x K16
+
+template <int NMMA>
+struct UpdCfg {
+  static constexpr int kTileB = NMMA * tc::kTileRowBytes;
+  static constexpr int kMaxSlices = kMaxSmall / 8;        // K = 2m <= 144
+  static constexpr int kBBytes = kDig * kMaxSlices * kTileB;
+  static constexpr int kSmem = kBBytes + kUpdSlots * kUpdSliceBytes + 1024;
+};
+
+// FP64 value of T * 2^(sh) for a 64-bit integer T (round to nearest; 0 below the normal range).
+__device__ __forceinline__ double ll_to_double_scaled(long long T, int sh) {
+  if (T == 0) return 0.0;
+  const unsigned long long sign = T < 0 ? (1ull << 63) : 0ull;
+  unsigned long long U = T < 0 ? (unsigned long long)(-T) : (unsigned long long)T;
+  const int lz = __clzll((long long)U);
+  int top = 63 - lz;                       // position of the leading one
+  unsigned long long M;
+  if (top > 52) {
+    const int r = top - 52;
+    M = (U + (1ull << (r - 1))) >> r;      // may carry into bit 53
+    if (M >> 53) { M >>= 1; ++top; }
+  } else {
+    M = U << (52 - top);
+  }
+  const int e = top + sh + 1023;
+  if (e <= 0) return 0.0;
+  if (e >= 2047) return __longlong_as_double((long long)(sign | (0x7FFull << 52)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) |
+                                          (M & 0xFFFFFFFFFFFFFull)));
+}
+
+// round(x * 2^s) for |x 2^s| < 2^22 (exact when x 2^s is an integer)
+__device__ __forceinline__ int magic_int(float x, float scale) {
+  return __float_as_int(fmaf(x, scale, 12582912.0f)) - 0x4B400000;
+}
+
+template <int NMMA, bool SUB>
+__global__ void __launch_bounds__(kUpdThreads, 1)
+update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, const double2* C2,
+                 int cstride, int q, double2* out1, double2* out2, int nout, int* err) {
+  using Cfg = UpdCfg<NMMA>;
+  const int prob = blockIdx.y;
+  if (bt.active && !bt.active[prob]) return;
+  const int o = blockIdx.x % nout, slot = blockIdx.x / nout, nslots = gridDim.x / nout;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full_bar[kUpdSlots], empty_bar[kUpdSlots];
+  __shared__ __align__(8) unsigned long long accf_bar, acce_bar, done_bar;
+  __shared__ __align__(8) unsigned long long rxf_bar[kRxRing], rxe_bar[kRxRing];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ int rowexp[kRxRing][128];
+  __shared__ int colexpB[NMMA];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t poff = (size_t)prob * bt.pstride;
+  const double2* C = (o == 0 ? C1 : C2) + (size_t)prob * cstride;
+  double2* Y = (o == 0 ? out1 : out2) + poff;
+  const int nsl = (m + 7) / 8;                  // K16 slices (8 S columns each)
+  const long long ntiles = (N + 127) / 128;
+  unsigned char* Bt = smem;                     // [slice][digit] B tiles
+  unsigned char* ring = smem + Cfg::kBBytes;    // [slot][digit] A tiles
+
+  // ---- set-up: column scales and digits of B (from C), barriers, tensor memory ----
+  for (int i = threadIdx.x; i < (Cfg::kBBytes + kUpdSlots * kUpdSliceBytes) / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  for (int n = threadIdx.x; n < NMMA; n += blockDim.x) {
+    int mx = 0;
+    if (n < 2 * q) {
+      const int j = n >> 1;
+      for (int c = 0; c < m; ++c) {
+        const double2 v = C[(size_t)c * q + j];
+        const unsigned int hx = (unsigned int)(__double_as_longlong(v.x) >> 32);
+        const unsigned int hy = (unsigned int)(__double_as_longlong(v.y) >> 32);
+        mx = max(mx, (int)max((hx >> 20) & 0x7FFu, (hy >> 20) & 0x7FFu));
+      }
+    }
+    colexpB[n] = mx;
+  }
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < kUpdSlots; ++sl) {
+      tc::bar_init(tc::smem_u32(&full_bar[sl]), kUpdProd * 32);
+      tc::bar_init(tc::smem_u32(&empty_bar[sl]), 1);
+    }
+    tc::bar_init(tc::smem_u32(&accf_bar), 1);
+    tc::bar_init(tc::smem_u32(&acce_bar), kUpdEpi * 32);
+    tc::bar_init(tc::smem_u32(&done_bar), 1);
+    for (int i = 0; i < kRxRing; ++i) {
+      tc::bar_init(tc::smem_u32(&rxf_bar[i]), kUpdProd * 32);
+      tc::bar_init(tc::smem_u32(&rxe_bar[i]), kUpdEpi * 32);
+    }
+    tc::bar_init_fence();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  // B row n, K-elements 16 s + 8 h .. + 7 = S columns c = 8 s + 4 h + u (re, im interleaved):
+  // row 2j:   Re Y_j = sum_c Re S_c Re C_cj - Im S_c Im C_cj
+  // row 2j+1: Im Y_j = sum_c Re S_c Im C_cj + Im S_c Re C_cj
+  for (int it = threadIdx.x; it < 2 * q * nsl * 2; it += blockDim.x) {
+    const int h = it & 1, sl = (it >> 1) % nsl, n = (it >> 1) / nsl;
+    const int j = n >> 1;
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = 8 * sl + 4 * h + u;
+      double2 cv = make_double2(0.0, 0.0);
+      if (c < m) cv = C[(size_t)c * q + j];
+      if ((n & 1) == 0) { v[2 * u] = cv.x; v[2 * u + 1] = -cv.y; }
+      else { v[2 * u] = cv.y; v[2 * u + 1] = cv.x; }
+    }
+    store_digits8(v, colexpB[n], Bt + (size_t)sl * kDig * Cfg::kTileB, Cfg::kTileB,
+                  tile_off(n, h));
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(&tmem_base), 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp < kUpdProd) {
+    // ---- producers: thread (rho, hh) owns row rho of the tile and half of its columns;
+    // both halves of a row sit in one warp, so the row's scale is a shuffle away ----
+    const int rho = warp * 16 + (lane & 15), hh = lane >> 4;
+    int j = 0;                                  // slices produced so far (ring position)
+    int tcount = 0;
+    for (long long t = slot; t < ntiles && !*abort_v; t += nslots, ++tcount) {
+      const long long r = t * 128 + rho;
+      const bool live = r < N;
+      // pass 1: this row's largest exponent over all of S's columns
+      unsigned int mx = 0;
+      if (live) {
+        for (int c = hh; c < m; c += 2) {
+          const double2 v = reinterpret_cast<const double2*>(S.p[c / S.b])[poff + (size_t)(c % S.b) * N + r];
+          const unsigned int hx = (unsigned int)(__double_as_longlong(v.x) >> 32);
+          const unsigned int hy = (unsigned int)(__double_as_longlong(v.y) >> 32);
+          mx = max(mx, max((hx >> 20) & 0x7FFu, (hy >> 20) & 0x7FFu));
+        }
+      }
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+      const int maxb = (int)mx;
+      // the row scales travel to the epilogue through a ring of buffers
+      const int rb = tcount % kRxRing;
+      if (!wait_bounded(tc::smem_u32(&rxe_bar[rb]), (uint32_t)(((tcount / kRxRing) & 1) ^ 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (hh == 0) rowexp[rb][rho] = maxb;
+      tc::bar_arrive(tc::smem_u32(&rxf_bar[rb]));
+      // pass 2: slices of 8 columns (this thread: 4 columns, re and im, of its row)
+      bool ok = true;
+      for (int sl = 0; sl < nsl; ++sl, ++j) {
+        const int st = j % kUpdSlots;
+        if (!wait_bounded(tc::smem_u32(&empty_bar[st]), (uint32_t)(((j / kUpdSlots) & 1) ^ 1))) {
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = 8 * sl + 4 * hh + u;
+          double2 x = make_double2(0.0, 0.0);
+          if (live && c < m)
+            x = reinterpret_cast<const double2*>(S.p[c / S.b])[poff + (size_t)(c % S.b) * N + r];
+          v[2 * u] = x.x; v[2 * u + 1] = x.y;
+        }
+        store_digits8(v, maxb, ring + (size_t)st * kUpdSliceBytes, kTileA, tile_off(rho, hh));
+        tc::fence_async_smem();
+        tc::bar_arrive(tc::smem_u32(&full_bar[st]));
+      }
+      if (!ok) break;
+    }
+  } else if (warp == kUpdProd) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idn = tc::idesc_bf16(128, NMMA, false);
+      int j = 0, tcount = 0;
+      for (long long t = slot; t < ntiles && !*abort_v; t += nslots, ++tcount) {
+        if (tcount > 0 &&
+            !wait_bounded(tc::smem_u32(&acce_bar), (uint32_t)((tcount - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        bool started[kNumAcc] = {false, false, false, false, false, false};
+        bool ok = true;
+        for (int sl = 0; sl < nsl; ++sl, ++j) {
+          const int st = j % kUpdSlots;
+          if (!wait_bounded(tc::smem_u32(&full_bar[st]), (uint32_t)((j / kUpdSlots) & 1))) {
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t aBase = tc::smem_u32(ring + (size_t)st * kUpdSliceBytes);
+          const uint32_t bBase = tc::smem_u32(Bt + (size_t)sl * kDig * Cfg::kTileB);
+          for (int k = 0; k < kDig; ++k)
+            for (int l = 0; l < kDig; ++l) {
+              if (k + l + 2 > kMaxLvl) continue;
+              const int acc = acc_of_level(k + l + 2);
+              tc::mma_bf16(tmem + (uint32_t)(acc * NMMA), tc::sdesc(aBase + k * kTileA),
+                           tc::sdesc(bBase + l * Cfg::kTileB), idn, started[acc]);
+              started[acc] = true;
+            }
+          tc::mma_commit(tc::smem_u32(&empty_bar[st]));
+        }
+        if (!ok) break;
+        tc::mma_commit(tc::smem_u32(&accf_bar));
+      }
+      tc::mma_commit(tc::smem_u32(&done_bar));
+      wait_bounded(tc::smem_u32(&done_bar), 0);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: lanes are rows; FP64 assembly with integer arithmetic ----
+    const int qd = warp & 3;
+    const int rho = 32 * qd + lane;
+    int tcount = 0;
+    for (long long t = slot; t < ntiles && !*abort_v; t += nslots, ++tcount) {
+      if (!wait_bounded(tc::smem_u32(&accf_bar), (uint32_t)(tcount & 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      tc::fence_after_sync();
+      const long long r = t * 128 + rho;
+      const int rb = tcount % kRxRing;
+      if (!wait_bounded(tc::smem_u32(&rxf_bar[rb]), (uint32_t)((tcount / kRxRing) & 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      const int er = rowexp[rb][rho];
+      tc::bar_arrive(tc::smem_u32(&rxe_bar[rb]));
+      constexpr int G = NMMA / 8;
+      for (int g = 0; g < G; ++g) {
+        float a[kNumAcc][8];
+#pragma unroll
+        for (int ac = 0; ac < kNumAcc; ++ac)
+          tc::tmem_ld8(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(ac * NMMA + 8 * g), a[ac]);
+        tc::tmem_wait_ld();
+        if (g == G - 1) {
+          tc::fence_before_sync();
+          tc::bar_arrive(tc::smem_u32(&acce_bar));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          const int jc = (8 * g + u) >> 1;       // complex output column
+          if (jc >= q || r >= N) continue;
+          double val[2];
+#pragma unroll
+          for (int w = 0; w < 2; ++w) {
+            const int n = 8 * g + u + w;
+            const long long T =
+                ((long long)magic_int(a[0][u + w], 1.0f) << 35) +
+                ((long long)magic_int(a[1][u + w], 128.0f) << 28) +
+                ((long long)magic_int(a[2][u + w], 16384.0f) << 21) +
+                ((long long)magic_int(a[3][u + w], 2097152.0f) << 14) +
+                ((long long)magic_int(a[4][u + w], 268435456.0f) << 7) +
+                ((long long)magic_int(a[5][u + w], 8589934592.0f) << 2);
+            // value = T 2^-35 2^(Er + En - 12), E = maxb - 1022
+            const int en = colexpB[n];
+            val[w] = (er >= 2047 || en >= 2047) ? nan("")
+                                                 : ll_to_double_scaled(T, er + en - 2044 - 12 - 35);
+          }
+          double2* dst = Y + (size_t)jc * N + r;
+          if (SUB) {
+            const double2 old = *dst;
+            *dst = make_double2(old.x - val[0], old.y - val[1]);
+          } else {
+            *dst = make_double2(val[0], val[1]);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (*abort_v && threadIdx.x == 0) atomicExch(err, kErrTimeout);
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+  }
+  return n;
+}
+
+template <bool SPLIT, int NMMA>
+iwf_status launch_gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, int ma,
+                          int mb, long long N, double2* out, double* partial, int slots_cap,
+                          int* err, cudaStream_t s) {
+  using Cfg = GramCfg<SPLIT, NMMA>;
+  static bool attr[64] = {};
+  int dev = 0;
+  IWF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    IWF_CUDA(cudaFuncSetAttribute(gram_tc_kernel<SPLIT, NMMA>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+    attr[dev] = true;
+  }
+  const int z = SPLIT ? 2 : 1;
+  const long long chunks = (N + Cfg::kChunkRows - 1) / Cfg::kChunkRows;
+  long long want = std::max(1, sm_count() / (z * std::max(1, bt.nprob)));
+  want = std::min<long long>(want, std::max<long long>(1, chunks));
+  want = std::min<long long>(want, slots_cap);
+  const long long per = (chunks + want - 1) / want * Cfg::kChunkRows;
+  const int slots = (int)((N + per - 1) / per);
+  dim3 grid((unsigned)std::max(1, slots), (unsigned)bt.nprob, (unsigned)z);
+  gram_tc_kernel<SPLIT, NMMA><<<grid, kGramThreads, Cfg::kSmem, s>>>(bt, A, B, ma, mb, N, per,
+                                                                      partial, err);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  gram_tc_reduce<SPLIT><<<dim3((ma * mb + 255) / 256, bt.nprob), 256, 0, s>>>(
+      bt, partial, std::max(1, slots), ma, mb, out);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+template <int NMMA, bool SUB>
+iwf_status launch_update_tc(const Batch& bt, const BlockList& S, int m, long long N,
+                            const double2* C1, const double2* C2, int cstride, int q,
+                            double2* out1, double2* out2, int* err, cudaStream_t s) {
+  using Cfg = UpdCfg<NMMA>;
+  static bool attr[64] = {};
+  int dev = 0;
+  IWF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    IWF_CUDA(cudaFuncSetAttribute(update_tc_kernel<NMMA, SUB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+    attr[dev] = true;
+  }
+  const int nout = (!SUB && C2) ? 2 : 1;
+  const long long ntiles = (N + 127) / 128;
+  long long slots = std::max(1, sm_count() / (nout * std::max(1, bt.nprob)));
+  slots = std::min(slots, ntiles);
+  dim3 grid((unsigned)(slots * nout), (unsigned)bt.nprob);
+  update_tc_kernel<NMMA, SUB><<<grid, kUpdThreads, Cfg::kSmem, s>>>(bt, S, m, N, C1, C2, cstride,
+                                                                    q, out1, out2, nout, err);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+}  // namespace
+
+iwf_status colexp(const Batch& bt, const BlockList& A, long long N, int off, cudaStream_t s) {
+  const int m = A.nb * A.b;
+  int* exps = bt.exps + off;
+  // clear this operand's slots of every problem (fixed capacity 2 * kMaxSmall per problem)
+  IWF_CUDA(cudaMemset2DAsync(exps, sizeof(int) * 2 * kMaxSmall, 0, sizeof(int) * m, bt.nprob, s));
+  const long long blocks = std::max<long long>(1, std::min<long long>(64, (N + 4095) / 4096));
+  colexp_kernel<<<dim3((unsigned)blocks, (unsigned)m, (unsigned)bt.nprob), 256, 0, s>>>(
+      bt, A, N, exps);
+  IWF_CUDA(cudaGetLastError());
+  count_launch();
+  return IWF_OK;
+}
+
+iwf_status gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, long long N,
+                   double2* out, double* partial, int slots_cap, int* err, cudaStream_t s) {
+  const int ma = A.nb * A.b, mb = B.nb * B.b;
+  if (!bt.exps) return fail(IWF_ERR_ARG, "gram_tc: no exponent scratch");
+  IWF_TRY(colexp(bt, A, N, 0, s));
+  IWF_TRY(colexp(bt, B, N, kMaxSmall, s));
+  if (2 * ma <= 128 && 2 * mb <= 48)
+    return launch_gram_tc<false, 48>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
+  if (ma <= 128 && mb <= 32)
+    return launch_gram_tc<true, 32>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
+  if (ma <= 128 && mb <= 48)
+    return launch_gram_tc<true, 48>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
+  if (ma <= 128 && mb <= 80)
+    return launch_gram_tc<true, 80>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
+  return fail(IWF_ERR_ARG, "gram_tc: shape");
+}
+
+iwf_status update_tc(const Batch& bt, const BlockList& S, long long N, const double2* C1,
+                     const double2* C2, int cstride, int q, double2* out1, double2* out2,
+                     bool subtract, int* err, cudaStream_t s) {
+  const int m = S.nb * S.b;
+  if (m > kMaxSmall || q < 1 || q > kMaxBlock) return fail(IWF_ERR_ARG, "update_tc: shape");
+  const int nm = ((2 * q + 15) / 16) * 16;
+#define IWF_UPD(NM)                                                                        \
+  if (nm == NM) {                                                                          \
+    if (subtract)                                                                          \
+      return launch_update_tc<NM, true>(bt, S, m, N, C1, nullptr, cstride, q, out1, nullptr, \
+                                        err, s);                                           \
+    return launch_update_tc<NM, false>(bt, S, m, N, C1, C2, cstride, q, out1, out2, err, s); \
+  }
+  IWF_UPD(16) IWF_UPD(32) IWF_UPD(48)
+#undef IWF_UPD
+  return fail(IWF_ERR_ARG, "update_tc: shape");
+}
+
+}  // namespace iwf
