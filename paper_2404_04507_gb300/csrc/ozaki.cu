@@ -6,17 +6,20 @@
 // in block form).
 //
 // Slicing. Every value v of a group that shares one scale 2^E (a column of a Gram operand,
-// a row of an update operand; |v| < 2^E) becomes the 49-bit integer I = round(v 2^(48-E)),
-// written in balanced base-128 digits I = sum_k d_k 2^(49-7k), k = 1..7, |d_k| <= 64. Digit k
-// is stored as the bf16 value d_k 2^(-7(k-1)) (exact: at most 7 significant bits), so
+// a row of an update operand; |v| < 2^E) becomes the 56-bit integer I = round(v 2^(55-E)),
+// written in balanced base-128 digits I = sum_k d_k 2^(56-7k), k = 1..8, |d_k| <= 64. Digit k
+// is stored as the bf16 value D_k = d_k 2^(-7(k-1)) (exact: at most 7 significant bits), so
 // v = 2^(E-6) sum_k D_k. A product of two values expands into digit pairs (k, l); pairs of one
 // level k + l are integer multiples of one unit 2^(-7(k+l-2)). The tensor core multiplies
 // bf16 pairs exactly and adds them in fp32; with |d| <= 64 a level's sum over a bounded
 // number of rows stays below 2^24 units, so levels 2..6 each keep an exact fp32 accumulator
-// in tensor memory, and levels 7..9 share one (their rounding sits below 2^-52 of the
-// result). Pairs with k + l >= 10 are dropped (below 2^-50 of the scales' product, with
-// random sign: the digits are balanced). Exact level sums are moved into double-float
-// registers (Gram: every few hundred rows) or assembled into FP64 (update).
+// in tensor memory, and levels 7..10 share one (their rounding sits below 2^-56 of the
+// scales' product). Pairs with k + l >= 11 are dropped (below 2^-62). The one rounding that
+// matters is that of v to I: 2^-56 of the group's scale. Exact level sums are moved into
+// double-float registers (Gram: every few hundred rows) or assembled into FP64 (update).
+// Fifty-six bits rather than the fifty-three of FP64: a scale is the largest magnitude of a
+// whole column or row, and H~ amplifies the high-frequency rows of H~W, so errors relative
+// to the scales must sit well below the FP64 rounding of the entries that matter.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -29,36 +32,39 @@ namespace iwf {
 
 namespace {
 
-constexpr int kDig = 7;                 // digits per value
-constexpr int kMaxLvl = 9;              // pairs k + l <= 9
-constexpr int kNumAcc = 6;              // levels 2..6 exact, 7..9 shared
+constexpr int kDig = 8;                 // digits per value
+constexpr int kMaxLvl = 10;             // pairs k + l <= 10
+constexpr int kNumAcc = 6;              // levels 2..6 exact, 7..10 shared
 constexpr long long kTcSpin = 1LL << 22;  // bounded mbarrier waits (try_wait rounds)
 constexpr int kErrTimeout = 1;
+constexpr int kSmemCap = 227 * 1024;    // dynamic shared memory per CTA on this GPU
 
 __device__ __forceinline__ int acc_of_level(int lvl) { return lvl <= 6 ? lvl - 2 : 5; }
 
-// Balanced base-128 digits of round(v 2^(48-E)), where the group's largest biased exponent is
-// maxb (E = maxb - 1022). Zeros, denormals and values far below 2^E give zero digits.
-__device__ __forceinline__ void digits7(double v, int maxb, int (&d)[kDig]) {
+// Balanced base-128 digits of round(v 2^(55-E)), where the group's largest biased exponent is
+// maxb (E = maxb - 1022, so |v| < 2^E). Zeros, denormals and values far below 2^E give zero
+// digits; a value above the scale (maxb too small) is clamped to the top of the range.
+__device__ __forceinline__ void digits8(double v, int maxb, int (&d)[kDig]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((bits >> 52) & 0x7FF);
-  int s = 5 + maxb - e;
-  s = s < 5 ? 5 : s;
   long long I = 0;
-  if (e != 0 && s < 64) {
+  if (e != 0) {
     const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    I = (long long)((M + (1ull << (s - 1))) >> s);
+    const int s = maxb - e - 2;              // right shift of the 53-bit mantissa
+    if (s <= 0) I = (long long)(M << (-s > 2 ? 2 : -s));
+    else if (s < 64) I = (long long)((M + (1ull << (s - 1))) >> s);
     if (bits >> 63) I = -I;
   }
   long long r = I;
-  const int d1 = (int)((r + (1LL << 41)) >> 42); r -= (long long)d1 << 42;
-  const int d2 = (int)((r + (1LL << 34)) >> 35); r -= (long long)d2 << 35;
-  const int d3 = (int)((r + (1LL << 27)) >> 28); r -= (long long)d3 << 28;
+  const int d1 = (int)((r + (1LL << 48)) >> 49); r -= (long long)d1 << 49;
+  const int d2 = (int)((r + (1LL << 41)) >> 42); r -= (long long)d2 << 42;
+  const int d3 = (int)((r + (1LL << 34)) >> 35); r -= (long long)d3 << 35;
+  const int d4 = (int)((r + (1LL << 27)) >> 28); r -= (long long)d4 << 28;
   int q = (int)r;
-  const int d4 = (q + (1 << 20)) >> 21; q -= d4 << 21;
-  const int d5 = (q + (1 << 13)) >> 14; q -= d5 << 14;
-  const int d6 = (q + (1 << 6)) >> 7; q -= d6 << 7;
-  d[0] = d1; d[1] = d2; d[2] = d3; d[3] = d4; d[4] = d5; d[5] = d6; d[6] = q;
+  const int d5 = (q + (1 << 20)) >> 21; q -= d5 << 21;
+  const int d6 = (q + (1 << 13)) >> 14; q -= d6 << 14;
+  const int d7 = (q + (1 << 6)) >> 7; q -= d7 << 7;
+  d[0] = d1; d[1] = d2; d[2] = d3; d[3] = d4; d[4] = d5; d[5] = d6; d[6] = d7; d[7] = q;
 }
 
 // Bits of the float d * 2^(-7k) (|d| <= 64: exact, low 16 bits zero, so its top half is bf16).
@@ -72,15 +78,15 @@ __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
 }
 
 // Digits of 8 consecutive values of one group, written as the 16-byte K-row of one tile row
-// in each of the 7 digit tiles (tile k at base + k * tile_stride).
+// in each of the digit tiles (tile k at base + k * tile_stride).
 __device__ __forceinline__ void store_digits8(const double (&v)[8], int maxb, unsigned char* base,
                                               uint32_t tile_stride, uint32_t off) {
   uint32_t w[kDig][4];
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
     int a[kDig], b[kDig];
-    digits7(v[j], maxb, a);
-    digits7(v[j + 1], maxb, b);
+    digits8(v[j], maxb, a);
+    digits8(v[j + 1], maxb, b);
 #pragma unroll
     for (int k = 0; k < kDig; ++k) w[k][j / 2] = pack2(digit_bits(a[k], k), digit_bits(b[k], k));
   }
@@ -107,6 +113,20 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills zeros (src is not read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+__host__ __device__ constexpr int round8(int x) { return (x + 7) & ~7; }
+
 // ---------------------------------------------------------------------------------------
 // Column scales: exps[c] = largest biased FP64 exponent over the re and im parts of column c
 // (2047 when the column holds an Inf or NaN, 0 for a zero column). exps must start at 0.
@@ -128,40 +148,49 @@ __global__ void colexp_kernel(Batch bt, BlockList A, long long N, int* exps) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Gram kernel. Roles: warps 0..7 slice 16-row stages of A and B into the digit tiles; warp 8
-// issues the MMAs; warps 9..16 move the level accumulators into double-float running sums
-// every CHUNK rows and write the CTA's partial at the end.
-//   FULL (2 ma <= 128, 2 mb <= 80): D = [Ar; Ai]^T [Br, Bi] in one accumulator set
+// Gram kernel. Roles: warps 0..7 slice 16-row stages of A and B into the digit tiles (the
+// FP64 rows of the next stage are already on their way into a staging buffer by cp.async);
+// warp 8 issues the MMAs; warps 9..16 move the level accumulators into double-float running
+// sums every CHUNK rows and write the CTA's partial at the end.
+//   FULL (2 ma <= 128, 2 mb <= 48): D = [Ar; Ai]^T [Br, Bi] in one accumulator set
 //     (M = 2ma, N = 2mb); the reduction forms re = ArBr + AiBi, im = ArBi - AiBr.
 //   SPLIT (ma <= 128, mb <= 80): blockIdx.z = 0 accumulates ArBr + AiBi, z = 1 ArBi - AiBr.
+// Tiles hold only the rows in use (rounded to 8); the MMA (M = 128, N = NMMA) reads on into
+// the following tiles, whose values land in accumulator lanes and columns nobody reads.
 constexpr int kProdWarps = 8, kEpiWarps = 8;
 constexpr int kGramThreads = (kProdWarps + 1 + kEpiWarps) * 32;
-constexpr int kTileA = 128 * tc::kTileRowBytes;     // 4 KB: M = 128 rows x K16
+constexpr int kMaxStages = 4;
+constexpr int kGuard = 4096;             // tail room for the MMAs' reads past the last tile
 
-template <bool SPLIT, int NMMA>
-struct GramCfg {
-  static constexpr int kTileB = NMMA * tc::kTileRowBytes;
-  static constexpr int kATiles = SPLIT ? 2 : 1;    // Ar, Ai (SPLIT) or [Ar; Ai]
-  static constexpr int kBTiles = SPLIT ? 2 : 1;
-  static constexpr int kStageBytes = kDig * (kATiles * kTileA + kBTiles * kTileB);
-  static constexpr int kStages = SPLIT ? 2 : 4;
-  static constexpr int kChunkRows = SPLIT ? 256 : 512;   // level sums stay below 2^24
-  static constexpr int kSmem = kStages * kStageBytes + 1024;
+struct GramLayout {
+  int rowsA, rowsB, tileA, tileB, nTA, stage, items, staging;
+  __host__ __device__ GramLayout(bool split, int ma, int mb) {
+    rowsA = split ? ma : 2 * ma;
+    rowsB = split ? mb : 2 * mb;
+    tileA = round8(rowsA) * tc::kTileRowBytes;
+    tileB = round8(rowsB) * tc::kTileRowBytes;
+    nTA = split ? 2 : 1;
+    stage = kDig * nTA * (tileA + tileB);
+    items = 2 * (ma + mb);
+    staging = items * 128;
+  }
+  __host__ __device__ int smem(int S) const { return S * stage + 2 * staging + kGuard; }
 };
+
+template <bool SPLIT> __host__ __device__ constexpr int chunk_rows() { return SPLIT ? 256 : 512; }
 
 template <bool SPLIT, int NMMA>
 __global__ void __launch_bounds__(kGramThreads, 1)
 gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
-               long long rows_per_slot, double* partial, int* err) {
-  using Cfg = GramCfg<SPLIT, NMMA>;
-  constexpr int S = Cfg::kStages;
+               long long rows_per_slot, int S, double* partial, int* err) {
   const int prob = blockIdx.y, slot = blockIdx.x, z = SPLIT ? blockIdx.z : 0;
   if (bt.active && !bt.active[prob]) return;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long full_bar[S], empty_bar[S], accf_bar, acce_bar;
-  __shared__ __align__(8) unsigned long long done_bar;
+  __shared__ __align__(8) unsigned long long full_bar[kMaxStages], empty_bar[kMaxStages];
+  __shared__ __align__(8) unsigned long long accf_bar, acce_bar, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  const GramLayout Lo(SPLIT, ma, mb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t poff = (size_t)prob * bt.pstride;
   const int* expA = bt.exps + (size_t)prob * 2 * kMaxSmall;
@@ -170,12 +199,16 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
   const long long r_end = min(N, r_begin + rows_per_slot);
   const long long nrows = r_end > r_begin ? r_end - r_begin : 0;
   const int nstages = (int)((nrows + 15) / 16);
-  constexpr int kStagesPerChunk = Cfg::kChunkRows / 16;
+  constexpr int kStagesPerChunk = chunk_rows<SPLIT>() / 16;
   const int nchunks = (nstages + kStagesPerChunk - 1) / kStagesPerChunk;
+  unsigned char* staging = smem + (size_t)S * Lo.stage;
 
-  // zero every stage (padding rows of the tiles stay zero), barriers, tensor memory
-  for (int i = threadIdx.x; i < S * Cfg::kStageBytes / 16; i += blockDim.x)
+  // zero the digit stages and the guard (their reads past the tiles stay finite), barriers,
+  // tensor memory
+  for (int i = threadIdx.x; i < S * Lo.stage / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < kGuard / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(staging + 2 * Lo.staging)[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       tc::bar_init(tc::smem_u32(&full_bar[s]), kProdWarps * 32);
@@ -199,57 +232,79 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
   volatile int* abort_v = &abort_flag;
 
   if (warp < kProdWarps) {
-    // ---- producers: one item = (column, K half) of A or B, 8 rows x (re, im) ----
+    // ---- producers: item = (column, K half) of A or B, 8 rows x (re, im); this thread owns
+    // items tid and tid + 256 in every stage, so it only ever reads the staging slots it
+    // filled itself ----
     const int tid = threadIdx.x;
-    const int items = 2 * (ma + mb);
+    const auto col_of = [&](int it, bool& isA, int& c) -> const double2* {
+      const int cc = it >> 1;
+      isA = cc < ma;
+      c = isA ? cc : cc - ma;
+      const BlockList& L = isA ? A : B;
+      return reinterpret_cast<const double2*>(L.p[c / L.b]) + poff + (size_t)(c % L.b) * N;
+    };
+    const auto issue = [&](int j) {
+      const int buf = j & 1;
+      const long long r0 = r_begin + 16LL * j;
+      for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
+        bool isA; int c;
+        const double2* col = col_of(it, isA, c);
+        const uint32_t dst = tc::smem_u32(staging + (size_t)buf * Lo.staging + (size_t)it * 128);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long r = r0 + 8 * (it & 1) + u;
+          const bool in = r < r_end;
+          cp_async16(dst + 16 * u, col + (in ? r : r_begin), in ? 16 : 0);
+        }
+      }
+      cp_async_commit();
+    };
+    if (nstages > 0) issue(0);
     for (int j = 0; j < nstages; ++j) {
       const int st = j % S;
+      if (j + 1 < nstages) issue(j + 1);
+      else cp_async_commit();                      // an empty group keeps the count uniform
+      cp_async_wait1();                            // this thread's copies of stage j landed
       if (!wait_bounded(tc::smem_u32(&empty_bar[st]), (uint32_t)(((j / S) & 1) ^ 1))) {
         atomicExch(&abort_flag, 1);
         break;
       }
       if (*abort_v) break;
-      unsigned char* stage = smem + (size_t)st * Cfg::kStageBytes;
-      unsigned char* tA = stage;                                        // [kATiles][kDig] tiles
-      unsigned char* tB = stage + kDig * Cfg::kATiles * kTileA;          // [kBTiles][kDig] tiles
-      const long long r0 = r_begin + 16LL * j;
-      for (int it = tid; it < items; it += kProdWarps * 32) {
-        const int h = it & 1, cc = it >> 1;
-        const bool isA = cc < ma;
-        const int c = isA ? cc : cc - ma;
-        const BlockList& L = isA ? A : B;
-        const double2* col = reinterpret_cast<const double2*>(L.p[c / L.b]) + poff +
-                             (size_t)(c % L.b) * N;
+      unsigned char* stage = smem + (size_t)st * Lo.stage;
+      unsigned char* tA = stage;                                  // [nTA][kDig] tiles
+      unsigned char* tB = stage + (size_t)kDig * Lo.nTA * Lo.tileA;
+      for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
+        const int h = it & 1;
+        bool isA; int c;
+        col_of(it, isA, c);
+        const double2* sv = reinterpret_cast<const double2*>(staging + (size_t)(j & 1) * Lo.staging +
+                                                             (size_t)it * 128);
         double re[8], im[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const long long r = r0 + 8 * h + u;
-          double2 v = make_double2(0.0, 0.0);
-          if (r < r_end) v = col[r];
-          re[u] = v.x; im[u] = v.y;
-        }
+        for (int u = 0; u < 8; ++u) { const double2 v = sv[u]; re[u] = v.x; im[u] = v.y; }
         const int maxb = isA ? expA[c] : expB[c];
         if (isA) {
           if (SPLIT) {
-            store_digits8(re, maxb, tA, kTileA, tile_off(c, h));
-            store_digits8(im, maxb, tA + kDig * kTileA, kTileA, tile_off(c, h));
+            store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
+            store_digits8(im, maxb, tA + kDig * Lo.tileA, Lo.tileA, tile_off(c, h));
           } else {
-            store_digits8(re, maxb, tA, kTileA, tile_off(c, h));
-            store_digits8(im, maxb, tA, kTileA, tile_off(c + ma, h));
+            store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
+            store_digits8(im, maxb, tA, Lo.tileA, tile_off(c + ma, h));
           }
         } else {
           if (SPLIT) {
-            store_digits8(re, maxb, tB, Cfg::kTileB, tile_off(c, h));
-            store_digits8(im, maxb, tB + kDig * Cfg::kTileB, Cfg::kTileB, tile_off(c, h));
+            store_digits8(re, maxb, tB, Lo.tileB, tile_off(c, h));
+            store_digits8(im, maxb, tB + kDig * Lo.tileB, Lo.tileB, tile_off(c, h));
           } else {
-            store_digits8(re, maxb, tB, Cfg::kTileB, tile_off(c, h));
-            store_digits8(im, maxb, tB, Cfg::kTileB, tile_off(c + mb, h));
+            store_digits8(re, maxb, tB, Lo.tileB, tile_off(c, h));
+            store_digits8(im, maxb, tB, Lo.tileB, tile_off(c + mb, h));
           }
         }
       }
       tc::fence_async_smem();
       tc::bar_arrive(tc::smem_u32(&full_bar[st]));
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kProdWarps) {
     // ---- MMA issuer ----
     if (lane == 0) {
@@ -272,19 +327,19 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
           break;
         }
         tc::fence_after_sync();
-        const uint32_t sbase = tc::smem_u32(smem + (size_t)st * Cfg::kStageBytes);
-        const uint32_t aBase = sbase, bBase = sbase + kDig * Cfg::kATiles * kTileA;
+        const uint32_t aBase = tc::smem_u32(smem + (size_t)st * Lo.stage);
+        const uint32_t bBase = aBase + kDig * Lo.nTA * Lo.tileA;
         for (int k = 0; k < kDig; ++k) {
           for (int l = 0; l < kDig; ++l) {
             if (k + l + 2 > kMaxLvl) continue;
             const int acc = acc_of_level(k + l + 2);
             const uint32_t d = tmem + (uint32_t)(acc * NMMA);
             if (!SPLIT) {
-              tc::mma_bf16(d, tc::sdesc(aBase + k * kTileA), tc::sdesc(bBase + l * Cfg::kTileB),
+              tc::mma_bf16(d, tc::sdesc(aBase + k * Lo.tileA), tc::sdesc(bBase + l * Lo.tileB),
                            idn, started[acc]);
             } else {
-              const uint32_t ar = aBase + k * kTileA, ai = aBase + (kDig + k) * kTileA;
-              const uint32_t br = bBase + l * Cfg::kTileB, bi = bBase + (kDig + l) * Cfg::kTileB;
+              const uint32_t ar = aBase + k * Lo.tileA, ai = aBase + (kDig + k) * Lo.tileA;
+              const uint32_t br = bBase + l * Lo.tileB, bi = bBase + (kDig + l) * Lo.tileB;
               if (z == 0) {
                 tc::mma_bf16(d, tc::sdesc(ar), tc::sdesc(br), idn, started[acc]);
                 tc::mma_bf16(d, tc::sdesc(ai), tc::sdesc(bi), idn, true);
@@ -346,7 +401,7 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
       tc::bar_arrive(tc::smem_u32(&acce_bar));
     }
     // partial of this CTA: FULL rows 2ma x cols 2mb; SPLIT [z] rows ma x cols mb
-    const int Mrows = SPLIT ? ma : 2 * ma, Ncols = SPLIT ? mb : 2 * mb;
+    const int Mrows = Lo.rowsA, Ncols = Lo.rowsB;
     double* out = partial + (((size_t)prob * gridDim.x + slot) * (SPLIT ? 2 : 1) + z) *
                                 (size_t)(Mrows * Ncols);
     if (lane_row < Mrows) {
@@ -424,7 +479,8 @@ constexpr int kUpdProd = 8, kUpdEpi = 4;
 constexpr int kUpdThreads = (kUpdProd + 1 + kUpdEpi) * 32;
 constexpr int kUpdSlots = 3;
 constexpr int kRxRing = 2;                               // row-scale buffers in flight
-constexpr int kUpdSliceBytes = kDig * kTileA;            // 7 digit tiles of 128 rows x K16
+constexpr int kTileA = 128 * tc::kTileRowBytes;          // 4 KB: 128 rows x K16
+constexpr int kUpdSliceBytes = kDig * kTileA;            // digit tiles of one K16 slice
 
 template <int NMMA>
 struct UpdCfg {
@@ -456,7 +512,7 @@ __device__ __forceinline__ double ll_to_double_scaled(long long T, int sh) {
                                           (M & 0xFFFFFFFFFFFFFull)));
 }
 
-// round(x * 2^s) for |x 2^s| < 2^22 (exact when x 2^s is an integer)
+// round(x * scale) for |x scale| < 2^22 (exact when x scale is an integer)
 __device__ __forceinline__ int magic_int(float x, float scale) {
   return __float_as_int(fmaf(x, scale, 12582912.0f)) - 0x4B400000;
 }
@@ -551,19 +607,30 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
     // ---- producers: thread (rho, hh) owns row rho of the tile and half of its columns;
     // both halves of a row sit in one warp, so the row's scale is a shuffle away ----
     const int rho = warp * 16 + (lane & 15), hh = lane >> 4;
+    const auto ld = [&](int c, long long r) {
+      return reinterpret_cast<const double2*>(S.p[c / S.b])[poff + (size_t)(c % S.b) * N + r];
+    };
     int j = 0;                                  // slices produced so far (ring position)
     int tcount = 0;
     for (long long t = slot; t < ntiles && !*abort_v; t += nslots, ++tcount) {
       const long long r = t * 128 + rho;
       const bool live = r < N;
-      // pass 1: this row's largest exponent over all of S's columns
+      // pass 1: this row's largest exponent over all of S's columns, eight loads in flight
       unsigned int mx = 0;
       if (live) {
-        for (int c = hh; c < m; c += 2) {
-          const double2 v = reinterpret_cast<const double2*>(S.p[c / S.b])[poff + (size_t)(c % S.b) * N + r];
-          const unsigned int hx = (unsigned int)(__double_as_longlong(v.x) >> 32);
-          const unsigned int hy = (unsigned int)(__double_as_longlong(v.y) >> 32);
-          mx = max(mx, max((hx >> 20) & 0x7FFu, (hy >> 20) & 0x7FFu));
+        for (int c0 = hh; c0 < m; c0 += 16) {
+          double2 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int c = c0 + 2 * u;
+            v[u] = c < m ? ld(c, r) : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const unsigned int hx = (unsigned int)(__double_as_longlong(v[u].x) >> 32);
+            const unsigned int hy = (unsigned int)(__double_as_longlong(v[u].y) >> 32);
+            mx = max(mx, max((hx >> 20) & 0x7FFu, (hy >> 20) & 0x7FFu));
+          }
         }
       }
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
@@ -576,10 +643,22 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
       }
       if (hh == 0) rowexp[rb][rho] = maxb;
       tc::bar_arrive(tc::smem_u32(&rxf_bar[rb]));
-      // pass 2: slices of 8 columns (this thread: 4 columns, re and im, of its row)
+      // pass 2: slices of 8 columns (this thread: 4 columns, re and im, of its row); the next
+      // slice's values are loaded before this one is sliced
+      double2 cur[4], nxt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = 4 * hh + u;
+        cur[u] = (live && c < m) ? ld(c, r) : make_double2(0.0, 0.0);
+      }
       bool ok = true;
       for (int sl = 0; sl < nsl; ++sl, ++j) {
         const int st = j % kUpdSlots;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = 8 * (sl + 1) + 4 * hh + u;
+          nxt[u] = (live && c < m) ? ld(c, r) : make_double2(0.0, 0.0);
+        }
         if (!wait_bounded(tc::smem_u32(&empty_bar[st]), (uint32_t)(((j / kUpdSlots) & 1) ^ 1))) {
           atomicExch(&abort_flag, 1);
           ok = false;
@@ -587,16 +666,12 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
         }
         double v[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = 8 * sl + 4 * hh + u;
-          double2 x = make_double2(0.0, 0.0);
-          if (live && c < m)
-            x = reinterpret_cast<const double2*>(S.p[c / S.b])[poff + (size_t)(c % S.b) * N + r];
-          v[2 * u] = x.x; v[2 * u + 1] = x.y;
-        }
+        for (int u = 0; u < 4; ++u) { v[2 * u] = cur[u].x; v[2 * u + 1] = cur[u].y; }
         store_digits8(v, maxb, ring + (size_t)st * kUpdSliceBytes, kTileA, tile_off(rho, hh));
         tc::fence_async_smem();
         tc::bar_arrive(tc::smem_u32(&full_bar[st]));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = nxt[u];
       }
       if (!ok) break;
     }
@@ -678,13 +753,16 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
 #pragma unroll
           for (int w = 0; w < 2; ++w) {
             const int n = 8 * g + u + w;
+            // T = 2^35 sum of the level sums; the level-l sum is a multiple of 2^(-7(l-2))
+            // (levels 2..6) and below 2^22 of its unit; the shared levels 7..10 are rounded
+            // at 2^-32
             const long long T =
                 ((long long)magic_int(a[0][u + w], 1.0f) << 35) +
                 ((long long)magic_int(a[1][u + w], 128.0f) << 28) +
                 ((long long)magic_int(a[2][u + w], 16384.0f) << 21) +
                 ((long long)magic_int(a[3][u + w], 2097152.0f) << 14) +
                 ((long long)magic_int(a[4][u + w], 268435456.0f) << 7) +
-                ((long long)magic_int(a[5][u + w], 8589934592.0f) << 2);
+                ((long long)magic_int(a[5][u + w], 4294967296.0f) << 3);
             // value = T 2^-35 2^(Er + En - 12), E = maxb - 1022
             const int en = colexpB[n];
             val[w] = (er >= 2047 || en >= 2047) ? nan("")
@@ -725,25 +803,29 @@ template <bool SPLIT, int NMMA>
 iwf_status launch_gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, int ma,
                           int mb, long long N, double2* out, double* partial, int slots_cap,
                           int* err, cudaStream_t s) {
-  using Cfg = GramCfg<SPLIT, NMMA>;
   static bool attr[64] = {};
   int dev = 0;
   IWF_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr[dev]) {
     IWF_CUDA(cudaFuncSetAttribute(gram_tc_kernel<SPLIT, NMMA>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     attr[dev] = true;
   }
+  const GramLayout Lo(SPLIT, ma, mb);
+  int S = kMaxStages;
+  while (S > 2 && Lo.smem(S) > kSmemCap) --S;
+  if (Lo.smem(S) > kSmemCap) return fail(IWF_ERR_ARG, "gram_tc: tiles exceed shared memory");
   const int z = SPLIT ? 2 : 1;
-  const long long chunks = (N + Cfg::kChunkRows - 1) / Cfg::kChunkRows;
+  constexpr int F = chunk_rows<SPLIT>();
+  const long long chunks = (N + F - 1) / F;
   long long want = std::max(1, sm_count() / (z * std::max(1, bt.nprob)));
   want = std::min<long long>(want, std::max<long long>(1, chunks));
   want = std::min<long long>(want, slots_cap);
-  const long long per = (chunks + want - 1) / want * Cfg::kChunkRows;
+  const long long per = (chunks + want - 1) / want * F;
   const int slots = (int)((N + per - 1) / per);
   dim3 grid((unsigned)std::max(1, slots), (unsigned)bt.nprob, (unsigned)z);
-  gram_tc_kernel<SPLIT, NMMA><<<grid, kGramThreads, Cfg::kSmem, s>>>(bt, A, B, ma, mb, N, per,
-                                                                      partial, err);
+  gram_tc_kernel<SPLIT, NMMA><<<grid, kGramThreads, Lo.smem(S), s>>>(bt, A, B, ma, mb, N, per,
+                                                                      S, partial, err);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   gram_tc_reduce<SPLIT><<<dim3((ma * mb + 255) / 256, bt.nprob), 256, 0, s>>>(
