@@ -951,7 +951,8 @@ iwf_status gram(const Batch& bt, const BlockList& A, const BlockList& B, long lo
   if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram: too many columns");
   if (herm && ma != mb) return fail(IWF_ERR_ARG, "gram: a Hermitian product must be square");
   if (sizeof(T) == 8 && bt.engine == kEngineTensor)
-    return gram_tc(bt, A, B, N, out, reinterpret_cast<double*>(partial), slots_per_prob, bt.err, s);
+    return gram_tc(bt, A, B, N, out, reinterpret_cast<double*>(partial), slots_per_prob, bt.err, s,
+                   herm);
   int g = grid_for(N, kGramRows);
   if (g > slots_per_prob) g = slots_per_prob;
   const int U = (ma + kGramTx - 1) / kGramTx, V = (mb + kGramTx - 1) / kGramTx;

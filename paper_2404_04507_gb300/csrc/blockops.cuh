@@ -87,7 +87,8 @@ iwf_status random_block(void* X, long long N, int b, unsigned long long seed, cu
 // Tensor-core (Ozaki scheme I) versions of gram<double> and block_update<double> (ozaki.cu);
 // partial holds nprob x slots_cap x 2 kCapG doubles.
 iwf_status gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, long long N,
-                   double2* out, double* partial, int slots_cap, int* err, cudaStream_t s);
+                   double2* out, double* partial, int slots_cap, int* err, cudaStream_t s,
+                   bool herm);
 iwf_status update_tc(const Batch& bt, const BlockList& S, long long N, const double2* C1,
                      const double2* C2, int cstride, int q, double2* out1, double2* out2,
                      bool subtract, int* err, cudaStream_t s);

@@ -12,9 +12,9 @@
 // v = 2^(E-6) sum_k D_k. A product of two values expands into digit pairs (k, l); pairs of one
 // level k + l are integer multiples of one unit 2^(-7(k+l-2)). The tensor core multiplies
 // bf16 pairs exactly and adds them in fp32; with |d| <= 64 a level's sum over a bounded
-// number of rows stays below 2^24 units, so levels 2..6 each keep an exact fp32 accumulator
-// in tensor memory, and levels 7..10 share one (their rounding sits below 2^-56 of the
-// scales' product). Pairs with k + l >= 11 are dropped (below 2^-62). The one rounding that
+// number of rows stays below 2^24 units, so levels 2..6 are exact in their fp32 accumulators
+// in tensor memory (one per level), and the rounding of levels 7..10 sits below 2^-56 of the
+// scales' product. Pairs with k + l >= 11 are dropped (below 2^-62). The one rounding that
 // matters is that of v to I: 2^-56 of the group's scale. Exact level sums are moved into
 // double-float registers (Gram: every few hundred rows) or assembled into FP64 (update).
 // Fifty-six bits rather than the fifty-three of FP64: a scale is the largest magnitude of a
@@ -34,12 +34,10 @@ namespace {
 
 constexpr int kDig = 8;                 // digits per value
 constexpr int kMaxLvl = 10;             // pairs k + l <= 10
-constexpr int kNumAcc = 6;              // levels 2..6 exact, 7..10 shared
 constexpr long long kTcSpin = 1LL << 22;  // bounded mbarrier waits (try_wait rounds)
 constexpr int kErrTimeout = 1;
-constexpr int kSmemCap = 227 * 1024;    // dynamic shared memory per CTA on this GPU
-
-__device__ __forceinline__ int acc_of_level(int lvl) { return lvl <= 6 ? lvl - 2 : 5; }
+constexpr int kSmemCap = 227 * 1024 - 2048;  // dynamic shared memory per CTA (227 KB less the
+                                              // kernels' static shared memory)
 
 // Balanced base-128 digits of round(v 2^(55-E)), where the group's largest biased exponent is
 // maxb (E = maxb - 1022, so |v| < 2^E). Zeros, denormals and values far below 2^E give zero
@@ -148,49 +146,64 @@ __global__ void colexp_kernel(Batch bt, BlockList A, long long N, int* exps) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Gram kernel. Roles: warps 0..7 slice 16-row stages of A and B into the digit tiles (the
-// FP64 rows of the next stage are already on their way into a staging buffer by cp.async);
-// warp 8 issues the MMAs; warps 9..16 move the level accumulators into double-float running
-// sums every CHUNK rows and write the CTA's partial at the end.
-//   FULL (2 ma <= 128, 2 mb <= 48): D = [Ar; Ai]^T [Br, Bi] in one accumulator set
-//     (M = 2ma, N = 2mb); the reduction forms re = ArBr + AiBi, im = ArBi - AiBr.
-//   SPLIT (ma <= 128, mb <= 80): blockIdx.z = 0 accumulates ArBr + AiBi, z = 1 ArBi - AiBr.
-// Tiles hold only the rows in use (rounded to 8); the MMA (M = 128, N = NMMA) reads on into
-// the following tiles, whose values land in accumulator lanes and columns nobody reads.
+// Gram kernel. The product is cut into sub-Grams of at most 48 A columns and 24 B columns,
+// D = [Ar; Ai]^T [Br, Bi] (M = 2na <= 96 lanes, N = 2nb <= 48 columns per level), one per
+// blockIdx.z; for a Hermitian product the sub-Grams below the block diagonal are skipped and
+// mirrored by the reduction. Each level 2..10 has its own accumulator (N columns apart in
+// tensor memory), so for one A digit k the B digits l of consecutive levels k + l sit next
+// to each other along N and one MMA covers up to 256 / N of them.
+// Roles: warps 0..7 slice 16-row stages of A and B into the digit tiles (the FP64 rows of
+// the next stage are already on their way into a staging buffer by cp.async); warp 8 issues
+// the MMAs; warps 9..16 move the level accumulators into double-float running sums every
+// 512 rows and write the CTA's partial at the end.
+// A tiles hold only the rows in use (rounded to 8); the MMA (M = 128) reads on into the
+// following tiles, whose values land in accumulator lanes nobody reads.
 constexpr int kProdWarps = 8, kEpiWarps = 8;
 constexpr int kGramThreads = (kProdWarps + 1 + kEpiWarps) * 32;
 constexpr int kMaxStages = 4;
 constexpr int kGuard = 4096;             // tail room for the MMAs' reads past the last tile
+constexpr int kNumLvl = kMaxLvl - 1;     // accumulators, levels 2..10
+constexpr int kChunkRows = 512;          // a level sum over 512 rows stays below 2^24 units
+constexpr int kMaxSub = 12;
 
+struct SubGram { int a0, na, b0, nb, poff; };
+struct SubList {
+  SubGram s[kMaxSub];
+  int n;
+  int slot_size;        // doubles of one slot's partials, over all sub-Grams
+  int herm;
+};
+
+template <int NMMA>
 struct GramLayout {
-  int rowsA, rowsB, tileA, tileB, nTA, stage, items, staging;
-  __host__ __device__ GramLayout(bool split, int ma, int mb) {
-    rowsA = split ? ma : 2 * ma;
-    rowsB = split ? mb : 2 * mb;
+  int rowsA, rowsB, tileA, stage, items, staging;
+  __host__ __device__ GramLayout(int na, int nb) {
+    rowsA = 2 * na;
+    rowsB = 2 * nb;
     tileA = round8(rowsA) * tc::kTileRowBytes;
-    tileB = round8(rowsB) * tc::kTileRowBytes;
-    nTA = split ? 2 : 1;
-    stage = kDig * nTA * (tileA + tileB);
-    items = 2 * (ma + mb);
+    stage = kDig * (tileA + NMMA * tc::kTileRowBytes);
+    items = 2 * (na + nb);
     staging = items * 128;
   }
   __host__ __device__ int smem(int S) const { return S * stage + 2 * staging + kGuard; }
 };
 
-template <bool SPLIT> __host__ __device__ constexpr int chunk_rows() { return SPLIT ? 256 : 512; }
-
-template <bool SPLIT, int NMMA>
+template <int NMMA>
 __global__ void __launch_bounds__(kGramThreads, 1)
-gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
-               long long rows_per_slot, int S, double* partial, int* err) {
-  const int prob = blockIdx.y, slot = blockIdx.x, z = SPLIT ? blockIdx.z : 0;
+gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_per_slot, int S,
+               SubList subs, double* partial, int* err) {
+  constexpr int kTileB = NMMA * tc::kTileRowBytes;
+  constexpr int kMaxCat = 256 / NMMA < kDig ? 256 / NMMA : kDig;
+  const int prob = blockIdx.y, slot = blockIdx.x, sub = blockIdx.z;
   if (bt.active && !bt.active[prob]) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) unsigned long long accf_bar, acce_bar, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
-  const GramLayout Lo(SPLIT, ma, mb);
+  const SubGram sg = subs.s[sub];
+  const int na = sg.na, nb = sg.nb;
+  const GramLayout<NMMA> Lo(na, nb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t poff = (size_t)prob * bt.pstride;
   const int* expA = bt.exps + (size_t)prob * 2 * kMaxSmall;
@@ -199,12 +212,12 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
   const long long r_end = min(N, r_begin + rows_per_slot);
   const long long nrows = r_end > r_begin ? r_end - r_begin : 0;
   const int nstages = (int)((nrows + 15) / 16);
-  constexpr int kStagesPerChunk = chunk_rows<SPLIT>() / 16;
+  constexpr int kStagesPerChunk = kChunkRows / 16;
   const int nchunks = (nstages + kStagesPerChunk - 1) / kStagesPerChunk;
   unsigned char* staging = smem + (size_t)S * Lo.stage;
 
-  // zero the digit stages and the guard (their reads past the tiles stay finite), barriers,
-  // tensor memory
+  // zero the digit stages and the guard (B padding rows stay zero; reads past the tiles stay
+  // inside the allocation), barriers, tensor memory
   for (int i = threadIdx.x; i < S * Lo.stage / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   for (int i = threadIdx.x; i < kGuard / 16; i += blockDim.x)
@@ -238,10 +251,11 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
     const int tid = threadIdx.x;
     const auto col_of = [&](int it, bool& isA, int& c) -> const double2* {
       const int cc = it >> 1;
-      isA = cc < ma;
-      c = isA ? cc : cc - ma;
+      isA = cc < na;
+      c = isA ? cc : cc - na;
+      const int g = isA ? sg.a0 + c : sg.b0 + c;
       const BlockList& L = isA ? A : B;
-      return reinterpret_cast<const double2*>(L.p[c / L.b]) + poff + (size_t)(c % L.b) * N;
+      return reinterpret_cast<const double2*>(L.p[g / L.b]) + poff + (size_t)(g % L.b) * N;
     };
     const auto issue = [&](int j) {
       const int buf = j & 1;
@@ -270,9 +284,8 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
         break;
       }
       if (*abort_v) break;
-      unsigned char* stage = smem + (size_t)st * Lo.stage;
-      unsigned char* tA = stage;                                  // [nTA][kDig] tiles
-      unsigned char* tB = stage + (size_t)kDig * Lo.nTA * Lo.tileA;
+      unsigned char* tA = smem + (size_t)st * Lo.stage;           // [kDig] A tiles
+      unsigned char* tB = tA + (size_t)kDig * Lo.tileA;           // [kDig] B tiles
       for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
         const int h = it & 1;
         bool isA; int c;
@@ -282,23 +295,14 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
         double re[8], im[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) { const double2 v = sv[u]; re[u] = v.x; im[u] = v.y; }
-        const int maxb = isA ? expA[c] : expB[c];
         if (isA) {
-          if (SPLIT) {
-            store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
-            store_digits8(im, maxb, tA + kDig * Lo.tileA, Lo.tileA, tile_off(c, h));
-          } else {
-            store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
-            store_digits8(im, maxb, tA, Lo.tileA, tile_off(c + ma, h));
-          }
+          const int maxb = expA[sg.a0 + c];
+          store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
+          store_digits8(im, maxb, tA, Lo.tileA, tile_off(c + na, h));
         } else {
-          if (SPLIT) {
-            store_digits8(re, maxb, tB, Lo.tileB, tile_off(c, h));
-            store_digits8(im, maxb, tB + kDig * Lo.tileB, Lo.tileB, tile_off(c, h));
-          } else {
-            store_digits8(re, maxb, tB, Lo.tileB, tile_off(c, h));
-            store_digits8(im, maxb, tB, Lo.tileB, tile_off(c + mb, h));
-          }
+          const int maxb = expB[sg.b0 + c];
+          store_digits8(re, maxb, tB, kTileB, tile_off(c, h));
+          store_digits8(im, maxb, tB, kTileB, tile_off(c + nb, h));
         }
       }
       tc::fence_async_smem();
@@ -306,11 +310,10 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kProdWarps) {
-    // ---- MMA issuer ----
+    // ---- MMA issuer: for A digit k, B digits l = 1..min(8, 10 - k) in runs of levels whose
+    // accumulators are all fresh or all started ----
     if (lane == 0) {
-      const uint32_t idn = tc::idesc_bf16(128, NMMA, false);
-      const uint32_t idneg = tc::idesc_bf16(128, NMMA, true);
-      bool started[kNumAcc];
+      uint32_t started = 0;                        // bit (level - 2)
       for (int j = 0; j < nstages && !*abort_v; ++j) {
         const int st = j % S;
         const int chunk = j / kStagesPerChunk;
@@ -320,7 +323,7 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
             atomicExch(&abort_flag, 1);
             break;
           }
-          for (int a = 0; a < kNumAcc; ++a) started[a] = false;
+          started = 0;
         }
         if (!wait_bounded(tc::smem_u32(&full_bar[st]), (uint32_t)((j / S) & 1))) {
           atomicExch(&abort_flag, 1);
@@ -328,27 +331,22 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
         }
         tc::fence_after_sync();
         const uint32_t aBase = tc::smem_u32(smem + (size_t)st * Lo.stage);
-        const uint32_t bBase = aBase + kDig * Lo.nTA * Lo.tileA;
-        for (int k = 0; k < kDig; ++k) {
-          for (int l = 0; l < kDig; ++l) {
-            if (k + l + 2 > kMaxLvl) continue;
-            const int acc = acc_of_level(k + l + 2);
-            const uint32_t d = tmem + (uint32_t)(acc * NMMA);
-            if (!SPLIT) {
-              tc::mma_bf16(d, tc::sdesc(aBase + k * Lo.tileA), tc::sdesc(bBase + l * Lo.tileB),
-                           idn, started[acc]);
-            } else {
-              const uint32_t ar = aBase + k * Lo.tileA, ai = aBase + (kDig + k) * Lo.tileA;
-              const uint32_t br = bBase + l * Lo.tileB, bi = bBase + (kDig + l) * Lo.tileB;
-              if (z == 0) {
-                tc::mma_bf16(d, tc::sdesc(ar), tc::sdesc(br), idn, started[acc]);
-                tc::mma_bf16(d, tc::sdesc(ai), tc::sdesc(bi), idn, true);
-              } else {
-                tc::mma_bf16(d, tc::sdesc(ar), tc::sdesc(bi), idn, started[acc]);
-                tc::mma_bf16(d, tc::sdesc(ai), tc::sdesc(br), idneg, true);
-              }
-            }
-            started[acc] = true;
+        const uint64_t dA = tc::sdesc(aBase);
+        const uint64_t dB = tc::sdesc(aBase + kDig * Lo.tileA);
+#pragma unroll 1
+        for (int k = 1; k <= kDig; ++k) {
+          const int lmax = min(kDig, kMaxLvl - k);
+          const uint64_t da = dA + (uint64_t)(((k - 1) * Lo.tileA) >> 4);
+          int l = 1;
+          while (l <= lmax) {
+            const int l0 = l;
+            const uint32_t st0 = (started >> (k + l0 - 2)) & 1u;
+            while (l <= lmax && l - l0 < kMaxCat && ((started >> (k + l - 2)) & 1u) == st0) ++l;
+            const int n = l - l0;
+            tc::mma_bf16(tmem + (uint32_t)((k + l0 - 2) * NMMA), da,
+                         dB + (uint64_t)(((l0 - 1) * kTileB) >> 4),
+                         tc::idesc_bf16(128, n * NMMA, false), st0 != 0);
+            started |= ((1u << n) - 1u) << (k + l0 - 2);
           }
         }
         tc::mma_commit(tc::smem_u32(&empty_bar[st]));
@@ -372,27 +370,30 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
     float hi[GH * 8], lo[GH * 8];
 #pragma unroll
     for (int i = 0; i < GH * 8; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+    const bool live = 32 * q < Lo.rowsA;            // lanes beyond 2na hold garbage
     for (int c = 0; c < nchunks && !*abort_v; ++c) {
       if (!wait_bounded(tc::smem_u32(&accf_bar), (uint32_t)(c & 1))) {
         atomicExch(&abort_flag, 1);
         break;
       }
       tc::fence_after_sync();
+      if (live) {
 #pragma unroll
-      for (int gi = 0; gi < GH; ++gi) {
-        const int g = g0 + gi;
-        if (g < g1) {
+        for (int gi = 0; gi < GH; ++gi) {
+          const int g = g0 + gi;
+          if (g < g1) {
 #pragma unroll
-          for (int a = 0; a < kNumAcc; ++a) {
-            float v[8];
-            tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * NMMA + 8 * g), v);
-            tc::tmem_wait_ld();
+            for (int a = 0; a < kNumLvl; ++a) {
+              float v[8];
+              tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * NMMA + 8 * g), v);
+              tc::tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              float s, er;
-              two_sum(hi[gi * 8 + u], v[u], s, er);
-              hi[gi * 8 + u] = s;
-              lo[gi * 8 + u] += er;
+              for (int u = 0; u < 8; ++u) {
+                float s, er;
+                two_sum(hi[gi * 8 + u], v[u], s, er);
+                hi[gi * 8 + u] = s;
+                lo[gi * 8 + u] += er;
+              }
             }
           }
         }
@@ -400,11 +401,10 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
       tc::fence_before_sync();
       tc::bar_arrive(tc::smem_u32(&acce_bar));
     }
-    // partial of this CTA: FULL rows 2ma x cols 2mb; SPLIT [z] rows ma x cols mb
-    const int Mrows = Lo.rowsA, Ncols = Lo.rowsB;
-    double* out = partial + (((size_t)prob * gridDim.x + slot) * (SPLIT ? 2 : 1) + z) *
-                                (size_t)(Mrows * Ncols);
-    if (lane_row < Mrows) {
+    // partial of this CTA and sub-Gram: rows 2na x cols 2nb
+    const int Ncols = Lo.rowsB;
+    double* out = partial + ((size_t)prob * gridDim.x + slot) * subs.slot_size + sg.poff;
+    if (lane_row < Lo.rowsA) {
 #pragma unroll
       for (int gi = 0; gi < GH; ++gi) {
         const int g = g0 + gi;
@@ -426,44 +426,48 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, int ma, int mb, long long N,
   }
 }
 
-// G[prob] (ma x mb, row-major, complex double at out + prob * kCapG) from the slot partials,
-// with the column scales 2^(Ea + Eb - 12), E = maxb - 1022.
-template <bool SPLIT>
+// G[prob] (ma x mb, row-major, complex double at out + prob * kCapG) from the slot partials of
+// the sub-Grams, with the column scales 2^(Ea + Eb - 12), E = maxb - 1022. An entry of a
+// skipped (Hermitian) block is the conjugate of its mirror image.
 __global__ void gram_tc_reduce(Batch bt, const double* partial, int slots, int ma, int mb,
-                               double2* out) {
+                               SubList subs, double2* out) {
   const int prob = blockIdx.y;
   if (bt.active && !bt.active[prob]) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ma * mb) return;
-  const int a = e / mb, b = e % mb;
-  const int* expA = bt.exps + (size_t)prob * 2 * kMaxSmall;
-  const int* expB = expA + kMaxSmall;
-  const int ea = expA[a], eb = expB[b];
-  double re = 0.0, im = 0.0;
-  if (!SPLIT) {
-    const int Nc = 2 * mb;
-    const size_t sz = (size_t)(2 * ma) * Nc;
-    const double* p = partial + (size_t)prob * slots * sz;
-    for (int s = 0; s < slots; ++s, p += sz) {
-      re += p[(size_t)a * Nc + b] + p[(size_t)(a + ma) * Nc + b + mb];
-      im += p[(size_t)a * Nc + b + mb] - p[(size_t)(a + ma) * Nc + b];
+  int a = e / mb, b = e % mb;
+  int si = -1;
+  bool mirror = false;
+  for (int t = 0; t < subs.n && si < 0; ++t) {
+    const SubGram& g = subs.s[t];
+    if (a >= g.a0 && a < g.a0 + g.na && b >= g.b0 && b < g.b0 + g.nb) si = t;
+  }
+  if (si < 0 && subs.herm) {
+    for (int t = 0; t < subs.n && si < 0; ++t) {
+      const SubGram& g = subs.s[t];
+      if (b >= g.a0 && b < g.a0 + g.na && a >= g.b0 && a < g.b0 + g.nb) si = t;
     }
-  } else {
-    const size_t sz = (size_t)ma * mb;
-    const double* p = partial + (size_t)prob * slots * 2 * sz;
-    for (int s = 0; s < slots; ++s, p += 2 * sz) {
-      re += p[(size_t)a * mb + b];
-      im += p[sz + (size_t)a * mb + b];
+    mirror = true;
+    const int tmp = a; a = b; b = tmp;
+  }
+  double2 r = make_double2(nan(""), nan(""));
+  if (si >= 0) {
+    const SubGram g = subs.s[si];
+    const int ia = a - g.a0, ib = b - g.b0, Nc = 2 * g.nb;
+    const double* p = partial + (size_t)prob * slots * subs.slot_size + g.poff;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < slots; ++s, p += subs.slot_size) {
+      re += p[(size_t)ia * Nc + ib] + p[(size_t)(ia + g.na) * Nc + ib + g.nb];
+      im += p[(size_t)ia * Nc + ib + g.nb] - p[(size_t)(ia + g.na) * Nc + ib];
+    }
+    const int* expA = bt.exps + (size_t)prob * 2 * kMaxSmall;
+    const int ea = expA[a], eb = expA[kMaxSmall + b];
+    if (ea < 2047 && eb < 2047) {
+      const double sc = ldexp(1.0, ea + eb - 2044 - 12);
+      r = make_double2(re * sc, mirror ? -im * sc : im * sc);
     }
   }
-  double2 g;
-  if (ea >= 2047 || eb >= 2047) {
-    g = make_double2(nan(""), nan(""));
-  } else {
-    const double sc = ldexp(1.0, ea + eb - 2044 - 12);
-    g = make_double2(re * sc, im * sc);
-  }
-  out[(size_t)prob * kCapG + e] = g;
+  out[(size_t)prob * kCapG + e] = r;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -522,6 +526,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
 update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, const double2* C2,
                  int cstride, int q, double2* out1, double2* out2, int nout, int* err) {
   using Cfg = UpdCfg<NMMA>;
+  constexpr int kMaxCat = 256 / NMMA < kDig ? 256 / NMMA : kDig;
   const int prob = blockIdx.y;
   if (bt.active && !bt.active[prob]) return;
   const int o = blockIdx.x % nout, slot = blockIdx.x / nout, nslots = gridDim.x / nout;
@@ -686,7 +691,7 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
           atomicExch(&abort_flag, 1);
           break;
         }
-        bool started[kNumAcc] = {false, false, false, false, false, false};
+        uint32_t started = 0;                      // bit (level - 2)
         bool ok = true;
         for (int sl = 0; sl < nsl; ++sl, ++j) {
           const int st = j % kUpdSlots;
@@ -696,16 +701,25 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
             break;
           }
           tc::fence_after_sync();
-          const uint32_t aBase = tc::smem_u32(ring + (size_t)st * kUpdSliceBytes);
-          const uint32_t bBase = tc::smem_u32(Bt + (size_t)sl * kDig * Cfg::kTileB);
-          for (int k = 0; k < kDig; ++k)
-            for (int l = 0; l < kDig; ++l) {
-              if (k + l + 2 > kMaxLvl) continue;
-              const int acc = acc_of_level(k + l + 2);
-              tc::mma_bf16(tmem + (uint32_t)(acc * NMMA), tc::sdesc(aBase + k * kTileA),
-                           tc::sdesc(bBase + l * Cfg::kTileB), idn, started[acc]);
-              started[acc] = true;
+          const uint64_t dA = tc::sdesc(tc::smem_u32(ring + (size_t)st * kUpdSliceBytes));
+          const uint64_t dB = tc::sdesc(tc::smem_u32(Bt + (size_t)sl * kDig * Cfg::kTileB));
+          // for A digit k, B digits l of consecutive levels in one MMA (see the Gram kernel)
+#pragma unroll 1
+          for (int k = 1; k <= kDig; ++k) {
+            const int lmax = min(kDig, kMaxLvl - k);
+            const uint64_t da = dA + (uint64_t)(((k - 1) * kTileA) >> 4);
+            int l = 1;
+            while (l <= lmax) {
+              const int l0 = l;
+              const uint32_t st0 = (started >> (k + l0 - 2)) & 1u;
+              while (l <= lmax && l - l0 < kMaxCat && ((started >> (k + l - 2)) & 1u) == st0) ++l;
+              const int n = l - l0;
+              tc::mma_bf16(tmem + (uint32_t)((k + l0 - 2) * NMMA), da,
+                           dB + (uint64_t)(((l0 - 1) * Cfg::kTileB) >> 4),
+                           tc::idesc_bf16(128, n * NMMA, false), st0 != 0);
+              started |= ((1u << n) - 1u) << (k + l0 - 2);
             }
+          }
           tc::mma_commit(tc::smem_u32(&empty_bar[st]));
         }
         if (!ok) break;
@@ -736,15 +750,18 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
       tc::bar_arrive(tc::smem_u32(&rxe_bar[rb]));
       constexpr int G = NMMA / 8;
       for (int g = 0; g < G; ++g) {
-        float a[kNumAcc][8];
+        float a[kNumLvl][8];
 #pragma unroll
-        for (int ac = 0; ac < kNumAcc; ++ac)
+        for (int ac = 0; ac < kNumLvl; ++ac)
           tc::tmem_ld8(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(ac * NMMA + 8 * g), a[ac]);
         tc::tmem_wait_ld();
         if (g == G - 1) {
           tc::fence_before_sync();
           tc::bar_arrive(tc::smem_u32(&acce_bar));
         }
+        // levels 7..10 together (their rounding sits far below the result's last bit)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[5][u] = (a[5][u] + a[6][u]) + (a[7][u] + a[8][u]);
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
           const int jc = (8 * g + u) >> 1;       // complex output column
@@ -753,20 +770,25 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
 #pragma unroll
           for (int w = 0; w < 2; ++w) {
             const int n = 8 * g + u + w;
-            // T = 2^35 sum of the level sums; the level-l sum is a multiple of 2^(-7(l-2))
-            // (levels 2..6) and below 2^22 of its unit; the shared levels 7..10 are rounded
-            // at 2^-32
-            const long long T =
-                ((long long)magic_int(a[0][u + w], 1.0f) << 35) +
-                ((long long)magic_int(a[1][u + w], 128.0f) << 28) +
-                ((long long)magic_int(a[2][u + w], 16384.0f) << 21) +
-                ((long long)magic_int(a[3][u + w], 2097152.0f) << 14) +
-                ((long long)magic_int(a[4][u + w], 268435456.0f) << 7) +
-                ((long long)magic_int(a[5][u + w], 4294967296.0f) << 3);
-            // value = T 2^-35 2^(Er + En - 12), E = maxb - 1022
+            // Th = 2^28 x (levels 2..6): the level-l sum is an integer multiple of 2^(-7(l-2))
+            // below 2^22 of its unit, so Th is exact (below 2^48). The shared levels 7..10 are
+            // added at a finer unit 2^(-28-k), k as large as keeps the sum in 62 bits.
+            const long long Th =
+                ((long long)magic_int(a[0][u + w], 1.0f) << 28) +
+                ((long long)magic_int(a[1][u + w], 128.0f) << 21) +
+                ((long long)magic_int(a[2][u + w], 16384.0f) << 14) +
+                ((long long)magic_int(a[3][u + w], 2097152.0f) << 7) +
+                (long long)magic_int(a[4][u + w], 268435456.0f);
+            const unsigned long long ua = Th < 0 ? (unsigned long long)(-Th) : (unsigned long long)Th;
+            const int nb = 64 - __clzll((long long)ua);
+            const int k = min(21, 62 - nb);
+            const long long T = Th * (1LL << k) +
+                                __float2ll_rn(a[5][u + w] * __int_as_float((127 + 28 + k) << 23));
+            // value = T 2^(-28-k) 2^(Er + En - 12), E = maxb - 1022
             const int en = colexpB[n];
-            val[w] = (er >= 2047 || en >= 2047) ? nan("")
-                                                 : ll_to_double_scaled(T, er + en - 2044 - 12 - 35);
+            val[w] = (er >= 2047 || en >= 2047)
+                         ? nan("")
+                         : ll_to_double_scaled(T, er + en - 2044 - 12 - 28 - k);
           }
           double2* dst = Y + (size_t)jc * N + r;
           if (SUB) {
@@ -799,37 +821,42 @@ int sm_count() {
   return n;
 }
 
-template <bool SPLIT, int NMMA>
-iwf_status launch_gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, int ma,
-                          int mb, long long N, double2* out, double* partial, int slots_cap,
-                          int* err, cudaStream_t s) {
+template <int NMMA>
+iwf_status launch_gram_tc(const Batch& bt, const BlockList& A, const BlockList& B,
+                          const SubList& subs, int ma, int mb, long long N, double2* out,
+                          double* partial, long long partial_cap, int* err, cudaStream_t s) {
   static bool attr[64] = {};
   int dev = 0;
   IWF_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr[dev]) {
-    IWF_CUDA(cudaFuncSetAttribute(gram_tc_kernel<SPLIT, NMMA>,
+    IWF_CUDA(cudaFuncSetAttribute(gram_tc_kernel<NMMA>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     attr[dev] = true;
   }
-  const GramLayout Lo(SPLIT, ma, mb);
+  int na_max = 0, nb_max = 0;
+  for (int t = 0; t < subs.n; ++t) {
+    na_max = std::max(na_max, subs.s[t].na);
+    nb_max = std::max(nb_max, subs.s[t].nb);
+  }
+  // the shared-memory layout of the largest sub-Gram serves them all
+  const GramLayout<NMMA> Lo(na_max, nb_max);
   int S = kMaxStages;
   while (S > 2 && Lo.smem(S) > kSmemCap) --S;
   if (Lo.smem(S) > kSmemCap) return fail(IWF_ERR_ARG, "gram_tc: tiles exceed shared memory");
-  const int z = SPLIT ? 2 : 1;
-  constexpr int F = chunk_rows<SPLIT>();
-  const long long chunks = (N + F - 1) / F;
-  long long want = std::max(1, sm_count() / (z * std::max(1, bt.nprob)));
+  const long long chunks = (N + kChunkRows - 1) / kChunkRows;
+  long long want = std::max(1, sm_count() / (subs.n * std::max(1, bt.nprob)));
   want = std::min<long long>(want, std::max<long long>(1, chunks));
-  want = std::min<long long>(want, slots_cap);
-  const long long per = (chunks + want - 1) / want * F;
+  want = std::min<long long>(want, std::max<long long>(
+                                       1, partial_cap / ((long long)subs.slot_size * bt.nprob)));
+  const long long per = (chunks + want - 1) / want * kChunkRows;
   const int slots = (int)((N + per - 1) / per);
-  dim3 grid((unsigned)std::max(1, slots), (unsigned)bt.nprob, (unsigned)z);
-  gram_tc_kernel<SPLIT, NMMA><<<grid, kGramThreads, Lo.smem(S), s>>>(bt, A, B, ma, mb, N, per,
-                                                                      S, partial, err);
+  dim3 grid((unsigned)std::max(1, slots), (unsigned)bt.nprob, (unsigned)subs.n);
+  gram_tc_kernel<NMMA><<<grid, kGramThreads, Lo.smem(S), s>>>(bt, A, B, N, per, S, subs, partial,
+                                                              err);
   IWF_CUDA(cudaGetLastError());
   count_launch();
-  gram_tc_reduce<SPLIT><<<dim3((ma * mb + 255) / 256, bt.nprob), 256, 0, s>>>(
-      bt, partial, std::max(1, slots), ma, mb, out);
+  gram_tc_reduce<<<dim3((ma * mb + 255) / 256, bt.nprob), 256, 0, s>>>(
+      bt, partial, std::max(1, slots), ma, mb, subs, out);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
@@ -876,20 +903,35 @@ iwf_status colexp(const Batch& bt, const BlockList& A, long long N, int off, cud
 }
 
 iwf_status gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, long long N,
-                   double2* out, double* partial, int slots_cap, int* err, cudaStream_t s) {
+                   double2* out, double* partial, int slots_cap, int* err, cudaStream_t s,
+                   bool herm) {
   const int ma = A.nb * A.b, mb = B.nb * B.b;
   if (!bt.exps) return fail(IWF_ERR_ARG, "gram_tc: no exponent scratch");
+  if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram_tc: shape");
   IWF_TRY(colexp(bt, A, N, 0, s));
   IWF_TRY(colexp(bt, B, N, kMaxSmall, s));
-  if (2 * ma <= 128 && 2 * mb <= 48)
-    return launch_gram_tc<false, 48>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
-  if (ma <= 128 && mb <= 32)
-    return launch_gram_tc<true, 32>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
-  if (ma <= 128 && mb <= 48)
-    return launch_gram_tc<true, 48>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
-  if (ma <= 128 && mb <= 80)
-    return launch_gram_tc<true, 80>(bt, A, B, ma, mb, N, out, partial, slots_cap, err, s);
-  return fail(IWF_ERR_ARG, "gram_tc: shape");
+  // sub-Grams: A in blocks of 48 columns, B in blocks of 24 (the last ones shorter)
+  const int nA = (ma + 47) / 48, nB = (mb + 23) / 24;
+  SubList subs{};
+  subs.herm = herm ? 1 : 0;
+  int off = 0, nbmax = 0;
+  for (int i = 0; i < nA; ++i) {
+    const int a0 = 48 * i, a1 = std::min(ma, a0 + 48);
+    for (int j = 0; j < nB; ++j) {
+      const int b0 = 24 * j, b1 = std::min(mb, b0 + 24);
+      if (herm && a0 >= b1) continue;              // entirely below the diagonal: mirrored
+      if (subs.n >= kMaxSub) return fail(IWF_ERR_ARG, "gram_tc: too many sub-Grams");
+      subs.s[subs.n++] = SubGram{a0, a1 - a0, b0, b1 - b0, off};
+      off += 4 * (a1 - a0) * (b1 - b0);
+      nbmax = std::max(nbmax, b1 - b0);
+    }
+  }
+  subs.slot_size = off;
+  const long long cap = (long long)bt.nprob * slots_cap * 2 * kCapG;
+  const int nm = ((2 * nbmax + 15) / 16) * 16;
+  if (nm == 16) return launch_gram_tc<16>(bt, A, B, subs, ma, mb, N, out, partial, cap, err, s);
+  if (nm == 32) return launch_gram_tc<32>(bt, A, B, subs, ma, mb, N, out, partial, cap, err, s);
+  return launch_gram_tc<48>(bt, A, B, subs, ma, mb, N, out, partial, cap, err, s);
 }
 
 iwf_status update_tc(const Batch& bt, const BlockList& S, long long N, const double2* C1,
