@@ -40,37 +40,42 @@ constexpr int kSmemCap = 227 * 1024 - 2048;  // dynamic shared memory per CTA (2
                                               // kernels' static shared memory)
 
 // Balanced base-128 digits of round(v 2^(55-E)), where the group's largest biased exponent is
-// maxb (E = maxb - 1022, so |v| < 2^E). Zeros, denormals and values far below 2^E give zero
-// digits; a value above the scale (maxb too small) is clamped to the top of the range.
-__device__ __forceinline__ void digits8(double v, int maxb, int (&d)[kDig]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((bits >> 52) & 0x7FF);
+// maxb (E = maxb - 1022, so |v| < 2^E), as the bit patterns of the floats
+// D_k = d_k 2^(-7(k-1)), |d_k| <= 64 (at most 7 significant bits: the top half is bf16).
+// The scaling is an integer add to v's exponent field and the rounding one hardware
+// conversion to a 64-bit integer (measured faster here than a rounded shift of the mantissa in
+// integer arithmetic); the digits then come from two 28-bit halves in 32-bit arithmetic.
+// Zeros, denormals and values below 2^(E-56) give zero digits.
+__device__ __forceinline__ void digits8(double v, int maxb, uint32_t (&f)[kDig]) {
+  const long long bits = __double_as_longlong(v);
+  const int hi = (int)(bits >> 32);
+  const int e = (hi >> 20) & 0x7FF;
+  const int sh = 1077 - maxb;                     // v 2^(55-E) = v 2^(sh)
   long long I = 0;
-  if (e != 0) {
-    const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int s = maxb - e - 2;              // right shift of the 53-bit mantissa
-    if (s <= 0) I = (long long)(M << (-s > 2 ? 2 : -s));
-    else if (s < 64) I = (long long)((M + (1ull << (s - 1))) >> s);
-    if (bits >> 63) I = -I;
+  if (e != 0 && e + sh > 0)
+    I = __double2ll_rn(__hiloint2double(hi + (sh << 20), (int)bits));
+  // I = q 2^28 + r with r in [-2^27, 2^27)
+  const int r0 = ((int)((unsigned int)I << 4)) >> 4;
+  int q = (int)((I - r0) >> 28);
+  int r = r0;
+  int d[kDig];
+  d[0] = (q + (1 << 20)) >> 21; q -= d[0] << 21;
+  d[1] = (q + (1 << 13)) >> 14; q -= d[1] << 14;
+  d[2] = (q + (1 << 6)) >> 7;   q -= d[2] << 7;
+  d[3] = q;
+  d[4] = (r + (1 << 20)) >> 21; r -= d[4] << 21;
+  d[5] = (r + (1 << 13)) >> 14; r -= d[5] << 14;
+  d[6] = (r + (1 << 6)) >> 7;   r -= d[6] << 7;
+  d[7] = r;
+  // d 2^(-7k) exactly: add d to the bits of m = 1.5 2^(23-7k) (whose last place is 2^(-7k)),
+  // then subtract m
+#pragma unroll
+  for (int k = 0; k < kDig; ++k) {
+    const float m = __int_as_float(((150 - 7 * k) << 23) | 0x400000);
+    f[k] = __float_as_uint(__int_as_float(__float_as_int(m) + d[k]) - m);
   }
-  long long r = I;
-  const int d1 = (int)((r + (1LL << 48)) >> 49); r -= (long long)d1 << 49;
-  const int d2 = (int)((r + (1LL << 41)) >> 42); r -= (long long)d2 << 42;
-  const int d3 = (int)((r + (1LL << 34)) >> 35); r -= (long long)d3 << 35;
-  const int d4 = (int)((r + (1LL << 27)) >> 28); r -= (long long)d4 << 28;
-  int q = (int)r;
-  const int d5 = (q + (1 << 20)) >> 21; q -= d5 << 21;
-  const int d6 = (q + (1 << 13)) >> 14; q -= d6 << 14;
-  const int d7 = (q + (1 << 6)) >> 7; q -= d7 << 7;
-  d[0] = d1; d[1] = d2; d[2] = d3; d[3] = d4; d[4] = d5; d[5] = d6; d[6] = d7; d[7] = q;
 }
 
-// Bits of the float d * 2^(-7k) (|d| <= 64: exact, low 16 bits zero, so its top half is bf16).
-__device__ __forceinline__ uint32_t digit_bits(int d, int k) {
-  const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) *
-                  __int_as_float((127 - 7 * k) << 23);
-  return __float_as_uint(f);
-}
 __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
   return __byte_perm(lo, hi, 0x7632);
 }
@@ -82,11 +87,11 @@ __device__ __forceinline__ void store_digits8(const double (&v)[8], int maxb, un
   uint32_t w[kDig][4];
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
-    int a[kDig], b[kDig];
+    uint32_t a[kDig], b[kDig];
     digits8(v[j], maxb, a);
     digits8(v[j + 1], maxb, b);
 #pragma unroll
-    for (int k = 0; k < kDig; ++k) w[k][j / 2] = pack2(digit_bits(a[k], k), digit_bits(b[k], k));
+    for (int k = 0; k < kDig; ++k) w[k][j / 2] = pack2(a[k], b[k]);
   }
 #pragma unroll
   for (int k = 0; k < kDig; ++k)
@@ -94,10 +99,7 @@ __device__ __forceinline__ void store_digits8(const double (&v)[8], int maxb, un
         make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
 }
 
-// Offset of (tile row rho, K half h) in a no-swizzle K-major K16 tile.
-__device__ __forceinline__ uint32_t tile_off(int rho, int h) {
-  return (uint32_t)((rho >> 3) * tc::kSBO + h * tc::kLBO + (rho & 7) * 16);
-}
+using tc::tile_off;
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -108,6 +110,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
   for (long long r = 0; r < kTcSpin; ++r)
     if (tc::bar_try_wait(bar, parity)) return true;
+  return false;
+}
+// The same for waits that usually last many microseconds (the accumulator hand-over): the
+// warp sleeps between polls instead of taking issue slots from the slicing warps. Bounded by
+// the same number of polls (about a second at the 256 ns sleep).
+__device__ __forceinline__ bool wait_bounded_sleep(uint32_t bar, uint32_t parity) {
+  for (long long r = 0; r < kTcSpin; ++r) {
+    if (tc::bar_try_wait(bar, parity)) return true;
+    __nanosleep(256);
+  }
   return false;
 }
 
@@ -124,6 +136,33 @@ __device__ __forceinline__ void cp_async_wait1() {
 }
 
 __host__ __device__ constexpr int round8(int x) { return (x + 7) & ~7; }
+
+
+// The MMAs of one K16 step, for A digits k and runs of B digits l0..l0+n-1 (consecutive levels
+// k + l, whose accumulators sit next to each other): entry = A tile index k - 1, B tile
+// index l0 - 1, first accumulator k + l0 - 2, run length n, and whether the run's
+// accumulators already hold partial sums. plan[0] is the first step of an accumulation
+// (every accumulator fresh), plan[1] any later step. Returns the number of entries of each.
+struct MmaStep { uint8_t a, b, acc, n, add; };
+constexpr int kMaxPlan = 24;
+__device__ __forceinline__ int make_plan(MmaStep* out, bool first, int max_cat) {
+  uint32_t started = first ? 0u : 0xFFFFFFFFu;
+  int cnt = 0;
+  for (int k = 1; k <= kDig; ++k) {
+    const int lmax = min(kDig, kMaxLvl - k);
+    int l = 1;
+    while (l <= lmax) {
+      const int l0 = l;
+      const uint32_t st0 = (started >> (k + l0 - 2)) & 1u;
+      while (l <= lmax && l - l0 < max_cat && ((started >> (k + l - 2)) & 1u) == st0) ++l;
+      const int n = l - l0;
+      out[cnt++] = MmaStep{(uint8_t)(k - 1), (uint8_t)(l0 - 1), (uint8_t)(k + l0 - 2), (uint8_t)n,
+                           (uint8_t)st0};
+      started |= ((1u << n) - 1u) << (k + l0 - 2);
+    }
+  }
+  return cnt;
+}
 
 // ---------------------------------------------------------------------------------------
 // Column scales: exps[c] = largest biased FP64 exponent over the re and im parts of column c
@@ -158,9 +197,10 @@ __global__ void colexp_kernel(Batch bt, BlockList A, long long N, int* exps) {
 // 512 rows and write the CTA's partial at the end.
 // A tiles hold only the rows in use (rounded to 8); the MMA (M = 128) reads on into the
 // following tiles, whose values land in accumulator lanes nobody reads.
-constexpr int kProdWarps = 8, kEpiWarps = 8;
+constexpr int kProdWarps = 10, kEpiWarps = 8;
 constexpr int kGramThreads = (kProdWarps + 1 + kEpiWarps) * 32;
 constexpr int kMaxStages = 4;
+constexpr int kStageRows = 32;           // rows per stage: two K16 steps
 constexpr int kGuard = 4096;             // tail room for the MMAs' reads past the last tile
 constexpr int kNumLvl = kMaxLvl - 1;     // accumulators, levels 2..10
 constexpr int kChunkRows = 512;          // a level sum over 512 rows stays below 2^24 units
@@ -181,8 +221,9 @@ struct GramLayout {
     rowsA = 2 * na;
     rowsB = 2 * nb;
     tileA = round8(rowsA) * tc::kTileRowBytes;
-    stage = kDig * (tileA + NMMA * tc::kTileRowBytes);
-    items = 2 * (na + nb);
+    // [A tiles: K16 step t, digit k][B tiles: t, digit l]
+    stage = (kStageRows / 16) * kDig * (tileA + NMMA * tc::kTileRowBytes);
+    items = (kStageRows / 8) * (na + nb);   // (column, 8-row group)
     staging = items * 128;
   }
   __host__ __device__ int smem(int S) const { return S * stage + 2 * staging + kGuard; }
@@ -201,6 +242,8 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
   __shared__ __align__(8) unsigned long long accf_bar, acce_bar, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ MmaStep plan[2][kMaxPlan];
+  __shared__ int plan_n[2];
   const SubGram sg = subs.s[sub];
   const int na = sg.na, nb = sg.nb;
   const GramLayout<NMMA> Lo(na, nb);
@@ -211,8 +254,12 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
   const long long r_begin = (long long)slot * rows_per_slot;
   const long long r_end = min(N, r_begin + rows_per_slot);
   const long long nrows = r_end > r_begin ? r_end - r_begin : 0;
-  const int nstages = (int)((nrows + 15) / 16);
-  constexpr int kStagesPerChunk = kChunkRows / 16;
+  const int nstages = (int)((nrows + kStageRows - 1) / kStageRows);
+  constexpr int kStagesPerChunk = kChunkRows / kStageRows;
+  constexpr int kSteps = kStageRows / 16;
+  __shared__ int sexpA[48], sexpB[24];
+  for (int i = threadIdx.x; i < na; i += blockDim.x) sexpA[i] = expA[sg.a0 + i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) sexpB[i] = expB[sg.b0 + i];
   const int nchunks = (nstages + kStagesPerChunk - 1) / kStagesPerChunk;
   unsigned char* staging = smem + (size_t)S * Lo.stage;
 
@@ -232,6 +279,8 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
     tc::bar_init(tc::smem_u32(&done_bar), 1);
     tc::bar_init_fence();
     abort_flag = 0;
+    plan_n[0] = make_plan(plan[0], true, kMaxCat);
+    plan_n[1] = make_plan(plan[1], false, kMaxCat);
   }
   if (warp == 0) {
     tc::tmem_alloc(tc::smem_u32(&tmem_base), 512);
@@ -245,12 +294,16 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
   volatile int* abort_v = &abort_flag;
 
   if (warp < kProdWarps) {
-    // ---- producers: item = (column, K half) of A or B, 8 rows x (re, im); this thread owns
-    // items tid and tid + 256 in every stage, so it only ever reads the staging slots it
-    // filled itself ----
+    // ---- producers: item = (column, 8-row group) of A or B, 8 rows x (re, im); this thread
+    // owns the same items in every stage, so it only ever reads the staging slots it filled
+    // itself. Staging is [row u][item], so that a warp's reads are consecutive ----
+    // item it: K half h = it & 1, column cc = (it >> 1) % ncols, K16 step t = (it >> 1) / ncols,
+    // so that a warp's tile stores cover whole 256-byte atoms of one step
     const int tid = threadIdx.x;
+    const int ncols = na + nb;
+    const auto grp_of = [&](int it) { return 2 * ((it >> 1) / ncols) + (it & 1); };
     const auto col_of = [&](int it, bool& isA, int& c) -> const double2* {
-      const int cc = it >> 1;
+      const int cc = (it >> 1) % ncols;
       isA = cc < na;
       c = isA ? cc : cc - na;
       const int g = isA ? sg.a0 + c : sg.b0 + c;
@@ -259,16 +312,16 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
     };
     const auto issue = [&](int j) {
       const int buf = j & 1;
-      const long long r0 = r_begin + 16LL * j;
+      const long long r0 = r_begin + (long long)kStageRows * j;
       for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
         bool isA; int c;
         const double2* col = col_of(it, isA, c);
-        const uint32_t dst = tc::smem_u32(staging + (size_t)buf * Lo.staging + (size_t)it * 128);
+        const uint32_t dst = tc::smem_u32(staging + (size_t)buf * Lo.staging + (size_t)it * 16);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const long long r = r0 + 8 * (it & 1) + u;
+          const long long r = r0 + 8 * grp_of(it) + u;
           const bool in = r < r_end;
-          cp_async16(dst + 16 * u, col + (in ? r : r_begin), in ? 16 : 0);
+          cp_async16(dst + (uint32_t)(u * Lo.items * 16), col + (in ? r : r_begin), in ? 16 : 0);
         }
       }
       cp_async_commit();
@@ -284,23 +337,24 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
         break;
       }
       if (*abort_v) break;
-      unsigned char* tA = smem + (size_t)st * Lo.stage;           // [kDig] A tiles
-      unsigned char* tB = tA + (size_t)kDig * Lo.tileA;           // [kDig] B tiles
+      unsigned char* sA = smem + (size_t)st * Lo.stage;           // [kSteps][kDig] A tiles
+      unsigned char* sB = sA + (size_t)kSteps * kDig * Lo.tileA;  // [kSteps][kDig] B tiles
       for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
-        const int h = it & 1;
+        const int g = grp_of(it), t = g >> 1, h = g & 1;
         bool isA; int c;
         col_of(it, isA, c);
-        const double2* sv = reinterpret_cast<const double2*>(staging + (size_t)(j & 1) * Lo.staging +
-                                                             (size_t)it * 128);
+        const double2* sv = reinterpret_cast<const double2*>(staging + (size_t)(j & 1) * Lo.staging) + it;
         double re[8], im[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) { const double2 v = sv[u]; re[u] = v.x; im[u] = v.y; }
+        for (int u = 0; u < 8; ++u) { const double2 v = sv[u * Lo.items]; re[u] = v.x; im[u] = v.y; }
         if (isA) {
-          const int maxb = expA[sg.a0 + c];
+          unsigned char* tA = sA + (size_t)t * kDig * Lo.tileA;
+          const int maxb = sexpA[c];
           store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
           store_digits8(im, maxb, tA, Lo.tileA, tile_off(c + na, h));
         } else {
-          const int maxb = expB[sg.b0 + c];
+          unsigned char* tB = sB + (size_t)t * kDig * kTileB;
+          const int maxb = sexpB[c];
           store_digits8(re, maxb, tB, kTileB, tile_off(c, h));
           store_digits8(im, maxb, tB, kTileB, tile_off(c + nb, h));
         }
@@ -310,20 +364,17 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kProdWarps) {
-    // ---- MMA issuer: for A digit k, B digits l = 1..min(8, 10 - k) in runs of levels whose
-    // accumulators are all fresh or all started ----
+    // ---- MMA issuer: the precomputed plan of each K16 step ----
     if (lane == 0) {
-      uint32_t started = 0;                        // bit (level - 2)
+      const int n0 = plan_n[0], n1 = plan_n[1];
       for (int j = 0; j < nstages && !*abort_v; ++j) {
         const int st = j % S;
         const int chunk = j / kStagesPerChunk;
-        if (j % kStagesPerChunk == 0) {
-          if (chunk > 0 &&
-              !wait_bounded(tc::smem_u32(&acce_bar), (uint32_t)((chunk - 1) & 1))) {
-            atomicExch(&abort_flag, 1);
-            break;
-          }
-          started = 0;
+        const bool fresh = j % kStagesPerChunk == 0;
+        if (fresh && chunk > 0 &&
+            !wait_bounded(tc::smem_u32(&acce_bar), (uint32_t)((chunk - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
         }
         if (!wait_bounded(tc::smem_u32(&full_bar[st]), (uint32_t)((j / S) & 1))) {
           atomicExch(&abort_flag, 1);
@@ -331,22 +382,20 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
         }
         tc::fence_after_sync();
         const uint32_t aBase = tc::smem_u32(smem + (size_t)st * Lo.stage);
-        const uint64_t dA = tc::sdesc(aBase);
-        const uint64_t dB = tc::sdesc(aBase + kDig * Lo.tileA);
-#pragma unroll 1
-        for (int k = 1; k <= kDig; ++k) {
-          const int lmax = min(kDig, kMaxLvl - k);
-          const uint64_t da = dA + (uint64_t)(((k - 1) * Lo.tileA) >> 4);
-          int l = 1;
-          while (l <= lmax) {
-            const int l0 = l;
-            const uint32_t st0 = (started >> (k + l0 - 2)) & 1u;
-            while (l <= lmax && l - l0 < kMaxCat && ((started >> (k + l - 2)) & 1u) == st0) ++l;
-            const int n = l - l0;
-            tc::mma_bf16(tmem + (uint32_t)((k + l0 - 2) * NMMA), da,
-                         dB + (uint64_t)(((l0 - 1) * kTileB) >> 4),
-                         tc::idesc_bf16(128, n * NMMA, false), st0 != 0);
-            started |= ((1u << n) - 1u) << (k + l0 - 2);
+        const uint32_t bBase = aBase + kSteps * kDig * Lo.tileA;
+#pragma unroll
+        for (int t = 0; t < kSteps; ++t) {
+          const uint64_t dA = tc::sdesc(aBase + t * kDig * Lo.tileA);
+          const uint64_t dB = tc::sdesc(bBase + t * kDig * kTileB);
+          const int pi = (fresh && t == 0) ? 0 : 1;
+          const int cnt = pi ? n1 : n0;
+          const MmaStep* pl = plan[pi];
+#pragma unroll 4
+          for (int i = 0; i < cnt; ++i) {
+            const MmaStep m = pl[i];
+            tc::mma_bf16(tmem + (uint32_t)(m.acc * NMMA), dA + (uint64_t)((m.a * Lo.tileA) >> 4),
+                         dB + (uint64_t)((m.b * kTileB) >> 4),
+                         tc::idesc_bf16(128, m.n * NMMA, false), m.add != 0);
           }
         }
         tc::mma_commit(tc::smem_u32(&empty_bar[st]));
@@ -372,7 +421,7 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
     for (int i = 0; i < GH * 8; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
     const bool live = 32 * q < Lo.rowsA;            // lanes beyond 2na hold garbage
     for (int c = 0; c < nchunks && !*abort_v; ++c) {
-      if (!wait_bounded(tc::smem_u32(&accf_bar), (uint32_t)(c & 1))) {
+      if (!wait_bounded_sleep(tc::smem_u32(&accf_bar), (uint32_t)(c & 1))) {
         atomicExch(&abort_flag, 1);
         break;
       }
@@ -538,6 +587,8 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
   __shared__ int abort_flag;
   __shared__ int rowexp[kRxRing][128];
   __shared__ int colexpB[NMMA];
+  __shared__ MmaStep plan[2][kMaxPlan];
+  __shared__ int plan_n[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t poff = (size_t)prob * bt.pstride;
   const double2* C = (o == 0 ? C1 : C2) + (size_t)prob * cstride;
@@ -577,6 +628,8 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
     }
     tc::bar_init_fence();
     abort_flag = 0;
+    plan_n[0] = make_plan(plan[0], true, kMaxCat);
+    plan_n[1] = make_plan(plan[1], false, kMaxCat);
   }
   __syncthreads();
   // B row n, K-elements 16 s + 8 h .. + 7 = S columns c = 8 s + 4 h + u (re, im interleaved):
@@ -691,7 +744,6 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
           atomicExch(&abort_flag, 1);
           break;
         }
-        uint32_t started = 0;                      // bit (level - 2)
         bool ok = true;
         for (int sl = 0; sl < nsl; ++sl, ++j) {
           const int st = j % kUpdSlots;
@@ -703,22 +755,15 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
           tc::fence_after_sync();
           const uint64_t dA = tc::sdesc(tc::smem_u32(ring + (size_t)st * kUpdSliceBytes));
           const uint64_t dB = tc::sdesc(tc::smem_u32(Bt + (size_t)sl * kDig * Cfg::kTileB));
-          // for A digit k, B digits l of consecutive levels in one MMA (see the Gram kernel)
-#pragma unroll 1
-          for (int k = 1; k <= kDig; ++k) {
-            const int lmax = min(kDig, kMaxLvl - k);
-            const uint64_t da = dA + (uint64_t)(((k - 1) * kTileA) >> 4);
-            int l = 1;
-            while (l <= lmax) {
-              const int l0 = l;
-              const uint32_t st0 = (started >> (k + l0 - 2)) & 1u;
-              while (l <= lmax && l - l0 < kMaxCat && ((started >> (k + l - 2)) & 1u) == st0) ++l;
-              const int n = l - l0;
-              tc::mma_bf16(tmem + (uint32_t)((k + l0 - 2) * NMMA), da,
-                           dB + (uint64_t)(((l0 - 1) * Cfg::kTileB) >> 4),
-                           tc::idesc_bf16(128, n * NMMA, false), st0 != 0);
-              started |= ((1u << n) - 1u) << (k + l0 - 2);
-            }
+          const int pi = sl == 0 ? 0 : 1;
+          const int cnt = plan_n[pi];
+          const MmaStep* pl = plan[pi];
+#pragma unroll 4
+          for (int i = 0; i < cnt; ++i) {
+            const MmaStep m = pl[i];
+            tc::mma_bf16(tmem + (uint32_t)(m.acc * NMMA), dA + (uint64_t)((m.a * kTileA) >> 4),
+                         dB + (uint64_t)((m.b * Cfg::kTileB) >> 4),
+                         tc::idesc_bf16(128, m.n * NMMA, false), m.add != 0);
           }
           tc::mma_commit(tc::smem_u32(&empty_bar[st]));
         }
@@ -735,7 +780,7 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
     const int rho = 32 * qd + lane;
     int tcount = 0;
     for (long long t = slot; t < ntiles && !*abort_v; t += nslots, ++tcount) {
-      if (!wait_bounded(tc::smem_u32(&accf_bar), (uint32_t)(tcount & 1))) {
+      if (!wait_bounded_sleep(tc::smem_u32(&accf_bar), (uint32_t)(tcount & 1))) {
         atomicExch(&abort_flag, 1);
         break;
       }

@@ -2,11 +2,11 @@
 // tcgen05.mma with shared-memory operand descriptors, commits to mbarriers, tensor-memory
 // loads, and bounded mbarrier waits.
 //
-// Operand layout used throughout (the canonical K-major layout without swizzle): a tile of
-// R rows x 16 K-elements of bf16 is a sequence of 8-row groups of 256 bytes; inside a group
-// the K-elements 0..7 of row r sit at r*16 bytes and K-elements 8..15 at 128 + r*16 bytes.
-// The descriptor's leading-byte offset (between the two K halves) is 128, its stride-byte
-// offset (between 8-row groups) 256.
+// Operand layout used throughout (K-major, 32-byte swizzle): a tile of R rows x 16
+// K-elements of bf16 is a sequence of 8-row atoms of 256 bytes; row r of an atom holds its
+// K-elements 0..7 in 16-byte chunk (0 ^ s) and 8..15 in chunk (1 ^ s) of bytes
+// [32 r, 32 r + 32), s = (r >> 2) & 1. The descriptor's stride-byte offset (between atoms) is
+// 256; tiles start on 256-byte boundaries.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,22 +15,28 @@
 namespace iwf {
 namespace tc {
 
-constexpr uint32_t kLBO = 128;     // bytes between K-adjacent core matrices
-constexpr uint32_t kSBO = 256;     // bytes between M/N-adjacent 8-row groups
+constexpr uint32_t kSBO = 256;     // bytes between M/N-adjacent 8-row atoms
 constexpr uint32_t kTileRowBytes = 32;   // one row of a K16 tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor (tcgen05 format, version 1, no swizzle).
+// Shared-memory matrix descriptor (tcgen05 format, version 1, 32-byte swizzle; the leading
+// byte offset is unused when a row of the tile is one swizzle atom wide).
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)1 << 16;
   d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
   return d;
+}
+
+// Byte offset of (row rho, K half h) in a tile of this layout.
+__device__ __forceinline__ uint32_t tile_off(int rho, int h) {
+  return (uint32_t)((rho >> 3) * kSBO + (rho & 7) * 32 + ((h ^ ((rho >> 2) & 1)) << 4));
 }
 
 // Instruction descriptor of kind::f16: bf16 A and B (both K-major), f32 accumulator,
