@@ -176,6 +176,124 @@ def cpu_oracle_rate(pb, budget_s: float = 12.0, max_vectors: int = 64):
     return done * win.N / dt, done, dt
 
 
+def cpu_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_c_oracle_rate(pb, nvec: int = 8, reps: int = 2):
+    """The oracle's C/OpenMP direct convolution (oracle/capply.c) on every host core: points/s
+    of H~ psi over an nvec block of the workload, best of reps."""
+    import oracle as O
+    from oracle import capply
+    win = O.build_window(pb.P, pb.K, pb.L, method=pb.method)
+    Vg = O.grid_coefficients(pb.modes, pb.coef, win.lens)
+    X = np.asfortranarray(W.random_block(win.N, nvec, seed=123))
+    capply.apply(win, Vg, X[:, :1])
+    best = 1e30
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        capply.apply(win, Vg, X)
+        best = min(best, time.perf_counter() - t0)
+    return nvec * win.N / best, best
+
+
+def cpu_fft_rate(pb, nvec: int = 8, reps: int = 2):
+    """The paper's method on the CPU (Alg. 1 inside Sec. 4.1's apply): scatter to the K*
+    grid, inverse n-D FFT, times V, forward n-D FFT, gather and + Lambda psi, with scipy.fft on
+    every host core. Same operator as the oracle (checked on the first vector)."""
+    import scipy.fft as sfft
+    import oracle as O
+    from oracle import capply, transform
+    win = O.build_window(pb.P, pb.K, pb.L, method=pb.method)
+    Vgrid = transform.sample_parent(pb.modes, pb.coef, win.lens).real
+    idx = tuple(win.kstar.T)
+    X = W.random_block(win.N, nvec, seed=124)
+    workers = cpu_cores()
+    size = float(np.prod(win.lens))
+
+    def apply_fft(x):
+        G = np.zeros(win.lens, dtype=np.complex128)
+        G[idx] = x
+        U = sfft.ifftn(G, workers=workers) * size
+        return sfft.fftn(Vgrid * U, workers=workers)[idx] / size + win.lam * x
+
+    y0 = apply_fft(X[:, 0])
+    ref = capply.apply(win, O.grid_coefficients(pb.modes, pb.coef, win.lens), X[:, 0])
+    err = float(np.max(np.abs(y0 - ref)) / np.max(np.abs(ref)))
+    best = 1e30
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        for c in range(nvec):
+            apply_fft(X[:, c])
+        best = min(best, time.perf_counter() - t0)
+    return nvec * win.N / best, best, workers, err
+
+
+def cpu_solve(pb, nev: int, block: int, tol: float = 1e-10, maxit: int = 400, seed: int = 7):
+    """Time to nev eigenpairs on the CPU: scipy's LOBPCG on the oracle's C operator, shifted
+    by sigma (V + sigma >= 1) and preconditioned by Eq. precond, to residual tol."""
+    import warnings
+    import scipy.sparse.linalg as spla
+    import oracle as O
+    from oracle import capply
+    win = O.build_window(pb.P, pb.K, pb.L, method=pb.method)
+    Vg = O.grid_coefficients(pb.modes, pb.coef, win.lens)
+    sigma = O.potential_shift(Vg)
+    M = O.precond_diag(win, Vg, sigma)
+
+    def mv(x):
+        x = np.asarray(x, dtype=np.complex128).reshape(win.N, -1)
+        return capply.apply(win, Vg, x) + sigma * x
+    A = spla.LinearOperator((win.N, win.N), matvec=mv, matmat=mv, dtype=np.complex128)
+    P = spla.LinearOperator((win.N, win.N), dtype=np.complex128,
+                            matvec=lambda x: M * np.asarray(x).reshape(-1),
+                            matmat=lambda x: M[:, None] * np.asarray(x))
+    X0 = W.random_block(win.N, block, seed=seed)
+    t0 = time.perf_counter()
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        w, V, rnh = spla.lobpcg(A, X0, M=P, tol=tol, maxiter=maxit, largest=False,
+                                retResidualNormsHistory=True)
+    dt = time.perf_counter() - t0
+    order = np.argsort(w)[:nev]
+    R = mv(V[:, order]) - V[:, order] * w[order][None, :]
+    res = np.linalg.norm(R, axis=0)
+    return {"seconds": dt, "iters": len(rnh), "max_resid": float(np.max(res)),
+            "converged": bool(np.all(res <= tol)), "lambda_0": float(w[order][0] - sigma),
+            "N": int(win.N), "nev": nev, "block": block}
+
+
+def cpu_baselines(pb, sweep_budget_s: float = 10.0):
+    """CPU baselines on every host core (the oracle C apply, the FFT method, and LOBPCG
+    solves) for the bench line; about a minute of CPU work."""
+    cores = cpu_cores()
+    v_c, t_c = cpu_c_oracle_rate(pb)
+    v_f, t_f, workers, err_f = cpu_fft_rate(pb)
+    v_np, nv_np, t_np = cpu_oracle_rate(pb, budget_s=2.0, max_vectors=2)
+    solves = {"config1": cpu_solve(W.config_1d(), 8, 8),
+              "config2_16^4": cpu_solve(W.config_moire(eps=EPS, K=8, L=8), 16, 24)}
+    eps, phases, cut, kl = W.sweep_params(256, seed=4)
+    idx = [i for i in range(256) if kl[i] == 8][:8]
+    done, t0, conv = 0, time.perf_counter(), True
+    for i in idx:
+        r = cpu_solve(W.sweep_problem(eps[i], phases[i], 8), 16, 24)
+        done += 1
+        conv = conv and r["converged"]
+        if time.perf_counter() - t0 > sweep_budget_s:
+            break
+    dt = time.perf_counter() - t0
+    solves["sweep_16^4"] = {"problems": done, "seconds": dt, "solves_per_s": done / dt,
+                            "converged": conv, "sample": f"first {done} of problems {idx}"}
+    return {"value": v_c, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle C/OpenMP direct convolution, 8 vectors of the 32^4 block "
+                       f"({t_c:.3f} s), {cores} threads"),
+            "fft_method": {"value": v_f, "unit": UNIT, "workers": workers,
+                           "seconds_8_vectors": t_f, "rel_err_vs_oracle": err_f,
+                           "kind": "paper method on the CPU: scipy.fft n-D FFT apply"},
+            "numpy_1thread": {"value": v_np, "unit": UNIT, "vectors": nv_np, "seconds": t_np},
+            "solves": solves}
+
+
 SOLVE_RUNS = [("iwfpm_f64", "iwfpm", "f64"), ("iwfpm_mixed", "iwfpm", "c64"),
               ("pm_f64", "pm", "f64")]
 
@@ -246,23 +364,26 @@ def run_reference(args):
     if rank != 0:
         return 0
     pb = W.config_moire(eps=EPS)
+    nvec = 4
     for _ in range(args.warmup):
-        cpu_oracle_rate(pb, budget_s=0.0, max_vectors=1)
+        cpu_c_oracle_rate(pb, nvec=1, reps=1)
     vals, per = [], []
     for _ in range(args.steps):
-        v, nv, dt = cpu_oracle_rate(pb, budget_s=0.0, max_vectors=1)
+        v, dt = cpu_c_oracle_rate(pb, nvec=nvec, reps=1)
         vals.append(v)
         per.append(dt)
     value = float(np.median(vals))
-    sample = f"1 vector of the 32^4 grid per step ({pb.dof} points), numpy, 1 thread"
+    cores = cpu_cores()
+    sample = (f"{nvec} vectors of the 32^4 grid per step ({pb.dof} points each), the oracle's "
+              f"C/OpenMP direct convolution, {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(per)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "moire2d_32^4_f64_apply", "grid": [32, 32, 32, 32],
-                   "nvec_per_step": 1, "eps": EPS, "theta": "pi/6", "method": "iwfpm"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": {"workload": "moire2d_32^4_f64_block16_apply", "grid": [32, 32, 32, 32],
+                   "nvec_per_step": nvec, "eps": EPS, "theta": "pi/6", "method": "iwfpm"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -549,10 +670,7 @@ def run_ours(args):
         return 0
     cpu = None
     if not args.no_cpu_baseline:
-        rate, nv, dt = cpu_oracle_rate(pb)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nv} vector(s) of the 32^4 grid in {dt:.1f} s, numpy direct "
-                         f"convolution, 1 thread"}
+        cpu = cpu_baselines(pb)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
