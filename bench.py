@@ -359,6 +359,85 @@ def time_sweep(iwf, torch, local, count=8, KL=8, nev=16, block=24):
             "sample": f"problems {idx} of W.sweep_params(256, seed=4) with K = L = {KL}"}
 
 
+def _read_golden(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", name)
+    vals = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                vals.append(float(line))
+    return np.array(vals)
+
+
+def time_config3(iwf, torch, local, maxit=600):
+    """The 3D QSE as stated (16^6 = 16.8M DOF, eps = 3, 16 pairs, block 24, mixed precision)
+    to residual 1e-10; eigenvalue error against the exact spectrum (a Kronecker sum of three
+    256-point problems, tests/golden/config3_exact.txt, written from the oracle)."""
+    pb = W.config_3d()
+    plan = iwf.Plan(pb.P, pb.K, pb.L, device=local)
+    plan.set_potential(pb.modes, pb.coef)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev, X, res, info = plan.eigensolve(16, block=24, tol=1e-10, maxit=maxit, precision="c64",
+                                       seed=3, raise_noconv=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    exact = _read_golden("config3_exact.txt")
+    err = np.abs(ev - exact) / np.maximum(1.0, np.abs(exact))
+    del X
+    plan.close()
+    return {"N": int(16 ** 6), "nev": 16, "block": 24, "precision": "mixed", "eps": 3.0,
+            "seconds": dt, "iters": info["iters"], "iters_c64": info["iters_c64"],
+            "converged": bool(info["converged"]), "max_resid": info["max_resid"],
+            "max_rel_eig_err_vs_exact": float(np.max(err)),
+            "per_result_rel_err": [float(v) for v in err]}
+
+
+def time_batch_sweep(iwf, torch, local, count=256, single_sample=8):
+    """Config 4 as stated: 256 solves of the moire QSE with eps ~ U[0.1, 10], phases ~
+    U[0, 2pi)^4 and cutoff c ~ U[8, 20] -> K = L = floor(0.65 c + 1/2) (seed 4), 16 pairs to
+    residual 1e-10, mixed precision, through one iwf_batch_solve call (uneven windows:
+    (2K)^4 from 10^4 to 4.6 x 10^5 points). One-by-one solves are timed on a sample spread
+    over the window sizes."""
+    eps, phases, cut, kl = W.sweep_params(count, seed=4)
+    plans = []
+    for i in range(count):
+        pb = W.sweep_problem(eps[i], phases[i], int(kl[i]))
+        p = iwf.Plan(pb.P, pb.K, pb.L, device=local)
+        p.set_potential(pb.modes, pb.coef)
+        plans.append(p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev, _, res, iters, info = iwf.batch_solve(plans, 16, block=24, tol=1e-10, precision="c64",
+                                              seed=7, raise_noconv=False)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    order = np.argsort(kl, kind="stable")
+    pick = [int(order[int(round(j * (count - 1) / (single_sample - 1)))]) for j in range(single_sample)]
+    t_single = 0.0
+    for i in pick:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        plans[i].eigensolve(16, block=24, tol=1e-10, precision="c64", seed=7, raise_noconv=False)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t1
+    sizes = {int(k): int((2 * k) ** 4) for k in np.unique(kl)}
+    for p in plans:
+        p.close()
+    return {"problems": count, "K=L range": [int(kl.min()), int(kl.max())],
+            "dof_range": [int((2 * kl.min()) ** 4), int((2 * kl.max()) ** 4)],
+            "nev": 16, "block": 24, "tol": 1e-10, "precision": "mixed",
+            "batched": {"seconds": t_batch, "solves_per_s": count / t_batch,
+                        "converged": bool(info["converged"]),
+                        "max_resid": float(np.max(res)), "max_iters": int(np.max(iters)),
+                        "call": "iwf_batch_solve (one call, plans grouped by window)"},
+            "one_by_one_sample": {"problems": single_sample, "seconds": t_single,
+                                  "solves_per_s": single_sample / t_single,
+                                  "sample": f"problems {pick} (spread over K = L)"},
+            "windows": {str(k): int(np.sum(kl == k)) for k in sizes}}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -663,6 +742,8 @@ def run_ours(args):
 
     solve = None if args.no_solve else time_solves(iwf, torch, local)
     sweep = None if (args.no_solve or args.no_sweep) else time_sweep(iwf, torch, local)
+    config3 = None if (args.no_solve or args.no_config3) else time_config3(iwf, torch, local)
+    sweep256 = None if (args.no_solve or args.no_sweep) else time_batch_sweep(iwf, torch, local)
 
     if rank != 0:
         if ws > 1:
@@ -684,6 +765,8 @@ def run_ours(args):
         "evaluate": evaluate,
         "solve": solve,
         "sweep": sweep,
+        "config3": config3,
+        "sweep256": sweep256,
     }
     print(json.dumps(line))
     if ws > 1:
@@ -704,6 +787,8 @@ def main(argv=None):
                     help="use the known tuned apply schedule instead of autotuning")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the config-4 sweep subsample (batched vs one-by-one solves)")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 16^6 3D QSE solve (config 3)")
     ap.add_argument("--no-long", action="store_true",
                     help="skip the measurement of the long-axis (shared-memory FFT) apply")
     ap.add_argument("--no-evaluate", action="store_true",

@@ -216,6 +216,32 @@ iwf_status iwf_batch_eigensolve(iwf_plan* plan, int nprob, const int* nmodes, co
                                 int* iters, iwf_solve_info* info, void* stream);
 
 /*
+ * Lowest nev eigenpairs of nplans independent problems, each given by its own plan (its own
+ * window K, L, method and potential: for example a sweep over potential strengths, phases
+ * and window cutoffs with uneven numbers of DOF). Each problem is Sec. 4.1's eigenproblem,
+ * solved by the method and options of iwf_eigensolve. Plans with the same P, K, L, method and
+ * shift form a group that advances in lockstep as one batch (as in iwf_batch_eigensolve);
+ * groups run side by side on their own streams, as many as fit in about 60 % of the free
+ * device memory, the largest first.
+ *   plans   host, nplans plan pointers, all on one device; every potential must be a sum of
+ *           single-axis modes (IWF_ERR_UNSUPPORTED otherwise). A plan may appear only once.
+ *   X0      host array of nplans device pointers (each N_p*block complex doubles) or NULL;
+ *           NULL entries (or X0 == NULL) take the seeded random start.
+ *   evals   host, nplans*nev (plan-major).   resid host, nplans*nev (may be NULL).
+ *   evecs   host array of nplans device pointers (each N_p*nev complex doubles, may be NULL),
+ *           or NULL.   iters host, nplans ints (may be NULL).
+ *   info    host (may be NULL): iters = the longest group's lockstep iterations, applies
+ *           summed, converged = all, max_resid over all, seconds = wall time of the call.
+ * The plans' workspaces are used: the caller must not apply with them meanwhile.
+ * Synchronises `stream` (every group starts after the work already on it).
+ * Errors: as iwf_eigensolve (IWF_ERR_NOCONV when some problem stopped at maxit; every
+ * output is still written).
+ */
+iwf_status iwf_batch_solve(int nplans, iwf_plan* const* plans, const iwf_solve_opts* opts,
+                           const void* const* X0, double* evals, void* const* evecs,
+                           double* resid, int* iters, iwf_solve_info* info, void* stream);
+
+/*
  * Learned warm start (no counterpart in the paper, whose start vector is e_1; Sec. 4.1):
  * an MLP from a potential's parameters to the lowest eigenvectors on a small "core" window.
  * Dense layers use bfloat16 weights and inputs with float32 accumulation on the tensor

@@ -10,7 +10,7 @@ import ctypes as C
 
 import numpy as np
 
-__all__ = ["Plan", "gram", "block_update"]
+__all__ = ["Plan", "gram", "block_update", "batch_solve"]
 
 
 def _torch():
@@ -371,6 +371,41 @@ class Plan:
             c.check(st, "iwf_batch_eigensolve")
         out = {f: getattr(info, f) for f, _ in c.iwf_solve_info._fields_}
         return evals, evecs, resid, iters, out
+
+
+def batch_solve(plans, nev, block=0, tol=1e-10, maxit=0, precision="f64", c64_tol=0.0,
+                seed=1, X0=None, want_vectors=False, stream=None, raise_noconv=True):
+    """iwf_batch_solve over independent plans (each with its own window and potential).
+
+    Returns (evals (nplans, nev), evecs list or None, resid, iters, info)."""
+    from . import capi
+    torch = _torch()
+    n = len(plans)
+    handles = (C.c_void_p * n)(*[p.handle.value for p in plans])
+    opts = capi.iwf_solve_opts(int(nev), int(block), int(maxit), float(tol),
+                               _solve_precision(capi, precision), float(c64_tol), int(seed))
+    evals = np.zeros((n, nev))
+    resid = np.zeros((n, nev))
+    iters = np.zeros(n, dtype=np.int32)
+    x0 = None
+    if X0 is not None:
+        x0 = (C.c_void_p * n)(*[(x.data_ptr() if x is not None else None) for x in X0])
+    vecs = None
+    vptr = None
+    if want_vectors:
+        vecs = [torch.empty((nev, p.N), dtype=torch.complex128, device=f"cuda:{p.device}")
+                for p in plans]
+        vptr = (C.c_void_p * n)(*[v.data_ptr() for v in vecs])
+    info = capi.iwf_solve_info()
+    st = capi.iwf_batch_solve(n, handles, C.byref(opts), x0,
+                              evals.ctypes.data_as(C.POINTER(C.c_double)), vptr,
+                              resid.ctypes.data_as(C.POINTER(C.c_double)),
+                              iters.ctypes.data_as(C.POINTER(C.c_int)), C.byref(info),
+                              Plan._stream(stream))
+    if st != 0 and not (st == -7 and not raise_noconv):
+        capi.check(st, "iwf_batch_solve")
+    out = {f: getattr(info, f) for f, _ in capi.iwf_solve_info._fields_}
+    return evals, vecs, resid, iters, out
 
 
 _ENGINES = {"tensor": 0, "df": 1, "f64": 2}

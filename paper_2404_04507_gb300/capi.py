@@ -100,6 +100,9 @@ _PROTOS = {
     "iwf_ws_embed": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
     "iwf_ws_phase": (_i, [_vp, _i, _i, C.POINTER(C.c_double), _i, _vp, _vp]),
     "iwf_plan_check": (_i, [_vp, _vp]),
+    "iwf_batch_solve": (_i, [_i, C.POINTER(_vp), C.POINTER(iwf_solve_opts), C.POINTER(_vp),
+                             C.POINTER(C.c_double), C.POINTER(_vp), C.POINTER(C.c_double),
+                             C.POINTER(_i), C.POINTER(iwf_solve_info), _vp]),
     "iwf_gram": (_i, [_i, _ll, _vp, _i, _vp, _i, _vp, _i, _vp]),
     "iwf_block_update": (_i, [_i, _ll, _vp, _i, _vp, _i, _vp, _i, _i, _vp]),
     "iwf_plan_set_wait_limit": (_i, [_vp, _ll]),

@@ -341,6 +341,14 @@ iwf_status iwf_batch_eigensolve(iwf_plan* p, int nprob, const int* nmodes, const
                                iters, info, (cudaStream_t)stream);
 }
 
+iwf_status iwf_batch_solve(int nplans, iwf_plan* const* plans, const iwf_solve_opts* opts,
+                           const void* const* X0, double* evals, void* const* evecs,
+                           double* resid, int* iters, iwf_solve_info* info, void* stream) {
+  clear_error();
+  return batch_solve_impl(nplans, plans, opts, X0, evals, evecs, resid, iters, info,
+                          (cudaStream_t)stream);
+}
+
 iwf_status iwf_eigensolve(iwf_plan* p, const iwf_solve_opts* opts, const void* X0, double* evals,
                           void* evecs, double* resid, iwf_solve_info* info, void* stream) {
   clear_error();

@@ -208,6 +208,9 @@ iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, cons
                                  const double* re, const double* im, const iwf_solve_opts* o,
                                  const void* X0, double* evals, void* evecs, double* resid,
                                  int* iters, iwf_solve_info* info, cudaStream_t st);
+iwf_status batch_solve_impl(int nplans, iwf_plan* const* plans, const iwf_solve_opts* o,
+                            const void* const* X0, double* evals, void* const* evecs,
+                            double* resid, int* iters, iwf_solve_info* info, cudaStream_t st);
 iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, int* best,
                          cudaStream_t stream);
 iwf_status set_schedule_impl(iwf_plan* p, int precision, int threads, int tile_kb, int chunk_mb);

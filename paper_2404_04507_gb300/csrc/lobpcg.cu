@@ -21,6 +21,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "blockops.cuh"
@@ -564,6 +568,195 @@ iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, cons
   IWF_CUDA(cudaMemcpyAsync(sm.off2, off2.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice, ss.s));
   ApplyBatch ab{tab64, tab32, stride, b, sm.active};
   return solve_problems(p, &ab, o, sm, ar, X0, evals, evecs, resid, iters, info, ss.s);
+}
+
+// ---------------------------------------------------------------------------------------
+// Many plans in one call. Plans with the same geometry (P, K, L, method, shift) form a group
+// that runs as one lockstep batch (per-problem potential tables, captured graphs); groups run
+// side by side on their own streams and host threads, as many at a time as fit in about 60 %
+// of the free device memory, largest first.
+namespace {
+
+bool same_geometry(const iwf_plan* a, const iwf_plan* b) {
+  if (a->device != b->device || a->method != b->method || a->shift_round != b->shift_round ||
+      a->g.d != b->g.d || a->g.n != b->g.n)
+    return false;
+  for (int j = 0; j < a->g.n; ++j)
+    if (a->g.lens[j] != b->g.lens[j]) return false;
+  return std::memcmp(a->P, b->P, sizeof(double) * a->g.d * a->g.n) == 0;
+}
+
+struct GroupJob {
+  std::vector<int> idx;        // plans of the group, in call order
+  size_t bytes = 0;            // device memory estimate of its solve
+  iwf_status st = IWF_OK;
+  std::string msg;
+  iwf_solve_info info{};
+};
+
+iwf_status run_group(iwf_plan* const* plans, GroupJob& job, const iwf_solve_opts* o,
+                     const void* const* X0, double* evals, void* const* evecs, double* resid,
+                     int* iters, cudaStream_t caller) {
+  iwf_plan* gp = plans[job.idx[0]];
+  DeviceGuard guard(gp->device);
+  const int np = (int)job.idx.size();
+  const int nev = o->nev;
+  const int b = o->block > 0 ? o->block : nev;
+  const long long N = gp->g.N;
+  IWF_TRY(check_opts(gp, o));
+  SolveStream ss;
+  IWF_TRY(ss.open(caller));
+  Arena ar;
+  Small sm;
+  IWF_TRY(alloc_small(ar, sm, np));
+  long long stride = 0;
+  for (int j = 0; j < gp->g.n; ++j) stride += gp->g.lens[j];
+  double* tab64;
+  float* tab32;
+  IWF_TRY(ar.get(&tab64, (size_t)np * stride));
+  IWF_TRY(ar.get(&tab32, (size_t)np * stride));
+  // each plan's per-axis tables, with its constant term folded into axis 0 (the batched
+  // apply's convention), and its preconditioner parameters
+  std::vector<double> t64((size_t)np * stride), shift(np), off2(np);
+  std::vector<float> t32((size_t)np * stride);
+  for (int q = 0; q < np; ++q) {
+    const iwf_plan* p = plans[job.idx[q]];
+    IWF_CUDA(cudaMemcpy(t64.data() + (size_t)q * stride, p->d_tab64, sizeof(double) * stride,
+                        cudaMemcpyDeviceToHost));
+    const double c = p->vconst / (double)N;
+    for (int l = 0; l < gp->g.lens[0]; ++l) t64[(size_t)q * stride + p->tab_off[0] + l] += c;
+    const double sigma = p->voff_abs - p->vg0 + 1.0;
+    shift[q] = p->vg0 + sigma;
+    off2[q] = p->voff_sq;
+  }
+  for (size_t i = 0; i < t64.size(); ++i) t32[i] = (float)t64[i];
+  IWF_CUDA(cudaMemcpyAsync(tab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, ss.s));
+  IWF_CUDA(cudaMemcpyAsync(tab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice, ss.s));
+  IWF_CUDA(cudaMemcpyAsync(sm.shift, shift.data(), sizeof(double) * np, cudaMemcpyHostToDevice, ss.s));
+  IWF_CUDA(cudaMemcpyAsync(sm.off2, off2.data(), sizeof(double) * np, cudaMemcpyHostToDevice, ss.s));
+  // start blocks: the caller's where given, else the seeded random block
+  double2* X0cat = nullptr;
+  bool any_x0 = false;
+  for (int q = 0; q < np && X0; ++q) any_x0 = any_x0 || X0[job.idx[q]] != nullptr;
+  if (any_x0) {
+    IWF_TRY(ar.get(&X0cat, (size_t)np * b * N));
+    for (int q = 0; q < np; ++q) {
+      double2* dst = X0cat + (size_t)q * b * N;
+      const void* src = X0[job.idx[q]];
+      if (src) IWF_CUDA(cudaMemcpyAsync(dst, src, sizeof(double2) * b * N, cudaMemcpyDeviceToDevice, ss.s));
+      else IWF_TRY(random_block<double>(dst, N, b, o->seed + 7919ull * (unsigned long long)q, ss.s));
+    }
+  }
+  double2* V = nullptr;
+  bool any_v = false;
+  for (int q = 0; q < np && evecs; ++q) any_v = any_v || evecs[job.idx[q]] != nullptr;
+  if (any_v) IWF_TRY(ar.get(&V, (size_t)np * nev * N));
+  std::vector<double> ev((size_t)np * nev), rs((size_t)np * nev);
+  std::vector<int> it(np);
+  ApplyBatch ab{tab64, tab32, stride, b, sm.active};
+  const iwf_status st = solve_problems(gp, &ab, o, sm, ar, X0cat, ev.data(), V, rs.data(),
+                                       it.data(), &job.info, ss.s);
+  if (st != IWF_OK && st != IWF_ERR_NOCONV) return st;
+  for (int q = 0; q < np; ++q) {
+    const int k = job.idx[q];
+    for (int j = 0; j < nev; ++j) {
+      evals[(size_t)k * nev + j] = ev[(size_t)q * nev + j];
+      if (resid) resid[(size_t)k * nev + j] = rs[(size_t)q * nev + j];
+    }
+    if (iters) iters[k] = it[q];
+    if (V && evecs[k])
+      IWF_CUDA(cudaMemcpyAsync(evecs[k], V + (size_t)q * nev * N, sizeof(double2) * nev * N,
+                               cudaMemcpyDeviceToDevice, ss.s));
+  }
+  IWF_CUDA(cudaStreamSynchronize(ss.s));
+  return st;
+}
+
+}  // namespace
+
+iwf_status batch_solve_impl(int nplans, iwf_plan* const* plans, const iwf_solve_opts* o,
+                            const void* const* X0, double* evals, void* const* evecs,
+                            double* resid, int* iters, iwf_solve_info* info,
+                            cudaStream_t st) {
+  if (nplans < 1 || !plans || !o || !evals) return fail(IWF_ERR_ARG, "iwf_batch_solve: bad arguments");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int nev = o->nev;
+  const int b = o->block > 0 ? o->block : nev;
+  std::vector<GroupJob> jobs;
+  for (int k = 0; k < nplans; ++k) {
+    iwf_plan* p = plans[k];
+    if (!p) return fail(IWF_ERR_ARG, "iwf_batch_solve: NULL plan");
+    if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_batch_solve: a plan has no potential");
+    if (p->pot_kind != 1)
+      return fail(IWF_ERR_UNSUPPORTED, "iwf_batch_solve: every potential must be a sum of "
+                                       "single-axis modes (per-axis tables)");
+    if (p->device != plans[0]->device)
+      return fail(IWF_ERR_ARG, "iwf_batch_solve: all plans must live on one device");
+    IWF_TRY(check_opts(p, o));
+    bool placed = false;
+    for (auto& j : jobs)
+      if (same_geometry(plans[j.idx[0]], p)) { j.idx.push_back(k); placed = true; break; }
+    if (!placed) { jobs.emplace_back(); jobs.back().idx.push_back(k); }
+  }
+  for (auto& j : jobs) {
+    const size_t N = (size_t)plans[j.idx[0]]->g.N;
+    // complex-double blocks (12) and, in the mixed mode, complex-float ones (11)
+    const size_t per = (size_t)b * N * (12 * 16 + (o->precision == IWF_PREC_C64 ? 11 * 8 : 0));
+    j.bytes = per * j.idx.size();
+    if ((long long)j.idx.size() * b > 65535) return fail(IWF_ERR_ARG, "iwf_batch_solve: a group exceeds 65535 vectors");
+  }
+  std::sort(jobs.begin(), jobs.end(), [](const GroupJob& a, const GroupJob& c) { return a.bytes > c.bytes; });
+  size_t free_b = 0, total_b = 0;
+  {
+    DeviceGuard guard(plans[0]->device);
+    IWF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  }
+  const size_t budget = (size_t)(0.6 * (double)free_b);
+  // launch groups while their estimates fit; the first one always runs
+  std::vector<std::thread> running;
+  std::vector<size_t> run_bytes;
+  size_t in_use = 0;
+  std::mutex mu;
+  size_t next = 0;
+  while (next < jobs.size() || !running.empty()) {
+    while (next < jobs.size() && (running.empty() || in_use + jobs[next].bytes <= budget)) {
+      GroupJob& j = jobs[next];
+      in_use += j.bytes;
+      running.emplace_back([&, jp = &j]() {
+        jp->st = run_group(plans, *jp, o, X0, evals, evecs, resid, iters, st);
+        if (jp->st != IWF_OK) jp->msg = iwf_last_error();
+      });
+      run_bytes.push_back(j.bytes);
+      ++next;
+    }
+    // wait for the oldest running group, then admit more
+    running.front().join();
+    in_use -= run_bytes.front();
+    running.erase(running.begin());
+    run_bytes.erase(run_bytes.begin());
+  }
+  iwf_status out = IWF_OK;
+  std::string msg;
+  long long applies = 0;
+  int max_it = 0, conv = 1;
+  double worst = 0.0;
+  for (const auto& j : jobs) {
+    if (j.st != IWF_OK && (out == IWF_OK || out == IWF_ERR_NOCONV)) { out = j.st; msg = j.msg; }
+    applies += j.info.applies;
+    max_it = std::max(max_it, j.info.iters);
+    conv = conv && j.info.converged;
+    worst = std::max(worst, j.info.max_resid);
+  }
+  if (info) {
+    info->iters = max_it;
+    info->iters_c64 = 0;
+    info->applies = applies;
+    info->converged = conv;
+    info->max_resid = worst;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (out != IWF_OK) return fail(out, msg);
+  return IWF_OK;
 }
 
 }  // namespace iwf

@@ -127,22 +127,23 @@ def test_eigensolve_argument_errors(iwf):
 
 
 @pytest.mark.parametrize("name", ["moire_ext", "pm_moire"])
-def test_double_float_contractions_match_fp64(iwf, name):
-    # "f64" runs the Gram products and block updates in double-float arithmetic on the FP32
-    # pipes, "f64_exact" in FP64: both must land on the dense oracle's eigenvalues and on each
-    # other to the solve tolerance, with residuals certified by the oracle's operator
+def test_contraction_engines_agree(iwf, name):
+    # "f64" runs the Gram products and block updates on the tensor cores (Ozaki scheme),
+    # "f64_df" in double-float arithmetic on the FP32 pipes, "f64_exact" in FP64: all three
+    # must land on the dense oracle's eigenvalues and on each other to the solve tolerance,
+    # with residuals certified by the oracle's operator
     pb = {"moire_ext": W.config_moire(eps=0.5, K=3, L=3),
           "pm_moire": W.config_moire(eps=0.5, K=3, L=3, method="pm")}[name]
     win = O.build_window(pb.P, pb.K, pb.L, method=pb.method)
     Vg = O.grid_coefficients(pb.modes, pb.coef, win.lens)
     ref = O.eigen.dense_eigs(win, Vg, 10)[0]
-    _, ev_df, X_df, _, info_df = _solve(iwf, pb, 10, 12, "f64")
-    _, ev_ex, _, _, info_ex = _solve(iwf, pb, 10, 12, "f64_exact")
-    assert info_df["converged"] == 1 and info_ex["converged"] == 1
-    assert _close(ev_df, ref) and _close(ev_ex, ref)
-    assert _close(ev_df, ev_ex)
-    r = O.eigen.residual_norms(win, Vg, X_df, ev_df)
-    assert np.max(r) <= 2e-10
+    out = {}
+    for prec in ("f64", "f64_df", "f64_exact"):
+        _, ev, X, _, info = _solve(iwf, pb, 10, 12, prec)
+        assert info["converged"] == 1 and _close(ev, ref), prec
+        assert np.max(O.eigen.residual_norms(win, Vg, X, ev)) <= 2e-10, prec
+        out[prec] = ev
+    assert _close(out["f64"], out["f64_exact"]) and _close(out["f64_df"], out["f64_exact"])
 
 
 def test_unknown_solver_precision_is_rejected(iwf):
@@ -167,5 +168,24 @@ def test_qse3d_kronecker_spectrum(iwf, precision):
     ref = O.eigen.kronecker_lowest([e1, e1, e1], 4)
     plan, ev, X, res, info = _solve(iwf, pb, 4, 12, precision)
     assert plan.N == 8 ** 6
+    assert info["converged"] == 1 and np.max(res) <= 1e-10
+    assert _close(ev, ref), np.max(np.abs(ev - ref))
+
+
+def test_qse3d_full_size_config3():
+    # the 3D QSE workload as stated (16^6 = 16.8M DOF, eps = 3, 16 pairs, block 24, mixed
+    # precision): eigenvalues within 1e-10 of the exact Kronecker-sum spectrum (three 1D
+    # problems P = [1, sqrt2], K = L = 8, 256-point dense eigenproblems), residuals <= 1e-10.
+    # The 16 lowest close a sixfold cluster (sizes 1, 3, 3, 3, 6).
+    import paper_2404_04507_gb300 as iwf
+    pb = W.config_3d()
+    m1, c1 = W.cosine_modes(2, 3.0)
+    w1 = O.build_window(np.array([[1.0, math.sqrt(2.0)]]), [8], [8])
+    e1 = O.eigen.dense_eigs(w1, O.grid_coefficients(m1, c1, w1.lens))[0]
+    ref = O.eigen.kronecker_lowest([e1, e1, e1], 16)
+    plan = iwf.Plan(pb.P, pb.K, pb.L)
+    plan.set_potential(pb.modes, pb.coef)
+    assert plan.N == 16 ** 6
+    ev, X, res, info = plan.eigensolve(16, block=24, precision="c64", maxit=600, seed=3)
     assert info["converged"] == 1 and np.max(res) <= 1e-10
     assert _close(ev, ref), np.max(np.abs(ev - ref))
