@@ -169,8 +169,10 @@ typedef struct {
  * Lowest nev eigenpairs of H~ (Sec. 4.1) by block LOBPCG (Alg. 2 in block form, Knyazev's
  * method cited there) with the diagonal preconditioner of Eq. precond, shifted as described
  * for iwf_preconditioner. Every step runs on the device: the FFT apply, the residual and
- * preconditioner, Gram products, orthonormalisation and the small Rayleigh-Ritz eigenproblem
- * (one-CTA Jacobi in FP64); the host reads only the residual norms once per iteration.
+ * preconditioner, Gram products and block updates (IWF_PREC_F64: tensor cores, FP64 values
+ * split into 56-bit fixed-point bf16 digits, Ozaki scheme), orthonormalisation and the small
+ * Rayleigh-Ritz eigenproblem (one-CTA Jacobi, FP64 angles, double-float rotations); the host
+ * reads only the residual norms once per iteration.
  *   X0     device, N*block complex doubles (window order, column-major) or NULL for a seeded
  *          random start (splitmix64 counter generator).
  *   evals  host, nev doubles, ascending.   resid host, nev doubles (may be NULL).
@@ -180,8 +182,9 @@ typedef struct {
  *          1e-12 once the projected matrix has large entries).
  *   evecs  device, N*nev complex doubles, orthonormal, column-major, window order.
  *   info   host (may be NULL).
- * The call allocates its workspace (about 12 blocks of N*block complex values) and
- * synchronises `stream` before returning.
+ * The workspace (about 12 blocks of N*block complex values) stays on the plan after the call,
+ * so a later solve of the same shape allocates nothing; iwf_plan_trim frees it. One solve at a
+ * time per plan. The call synchronises `stream` before returning.
  * Errors: IWF_ERR_ARG, IWF_ERR_ALLOC, IWF_ERR_CUDA, IWF_ERR_NONFINITE (a NaN or Inf in X0,
  * checked on the device before the first iteration, or a non-finite residual), IWF_ERR_TIMEOUT
  * (an apply gave up waiting for a copy, read at the per-iteration synchronisation),
@@ -208,7 +211,8 @@ iwf_status iwf_eigensolve(iwf_plan* plan, const iwf_solve_opts* opts, const void
  *   info    host (may be NULL): totals over the batch (iters = lockstep iterations).
  *   X0      device, nprob*block*N complex doubles (problem p's start block at p*block*N,
  *           column-major, window order) or NULL for the seeded random start.
- * nprob * block <= 65535. Synchronises `stream`.
+ * nprob * block <= 65535. The workspace stays on the plan, as for iwf_eigensolve.
+ * Synchronises `stream`.
  */
 iwf_status iwf_batch_eigensolve(iwf_plan* plan, int nprob, const int* nmodes, const int* m,
                                 const double* re, const double* im, const iwf_solve_opts* opts,
@@ -240,6 +244,14 @@ iwf_status iwf_batch_eigensolve(iwf_plan* plan, int nprob, const int* nmodes, co
 iwf_status iwf_batch_solve(int nplans, iwf_plan* const* plans, const iwf_solve_opts* opts,
                            const void* const* X0, double* evals, void* const* evecs,
                            double* resid, int* iters, iwf_solve_info* info, void* stream);
+
+/*
+ * Frees the eigensolver workspace that iwf_eigensolve and iwf_batch_eigensolve keep on the
+ * plan (iwf_batch_solve allocates its groups' workspaces per call and frees them before it
+ * returns). The plan stays usable; the next solve allocates again. Waits for the plan's
+ * device work (cudaFree). Library extension: the paper has no counterpart.
+ */
+void iwf_plan_trim(iwf_plan* plan);
 
 /*
  * Learned warm start (no counterpart in the paper, whose start vector is e_1; Sec. 4.1):

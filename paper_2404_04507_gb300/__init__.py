@@ -283,6 +283,10 @@ class Plan:
         return {"threads": out[0], "tile_kb": out[1], "chunk_mb": out[2],
                 "path": names[out[3]]}
 
+    def trim(self):
+        """iwf_plan_trim: free the eigensolver workspace kept on the plan between solves."""
+        self._c.iwf_plan_trim(self.handle)
+
     def check(self, stream=None):
         """iwf_plan_check: raises IwfError (IWF_ERR_TIMEOUT) if an apply on this plan gave up
         waiting since the last check; synchronises the stream."""

@@ -166,6 +166,13 @@ iwf_status iwf_plan_create(iwf_plan** plan, int d, int n, const double* P, const
   return plan_create(plan, d, n, P, K, L, opts);
 }
 
+void iwf_plan_trim(iwf_plan* p) {
+  if (!p) return;
+  DeviceGuard guard(p->device);
+  for (auto& b : p->solve_ws) cudaFree(b.ptr);
+  p->solve_ws.clear();
+}
+
 void iwf_plan_destroy(iwf_plan* p) {
   if (!p) return;
   DeviceGuard guard(p->device);
@@ -188,6 +195,7 @@ void iwf_plan_destroy(iwf_plan* p) {
   cudaFree(p->d_grid64);
   cudaFree(p->d_grid32);
   cudaFree(p->d_work);
+  for (auto& b : p->solve_ws) cudaFree(b.ptr);
   delete p;
 }
 

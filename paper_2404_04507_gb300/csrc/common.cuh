@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/iwfpm.h"
 
@@ -173,6 +174,10 @@ struct iwf_plan {
   // apply kernels per precision: IWF_PATH_AUTO (pencil path where the geometry allows it),
   // IWF_PATH_TILED or IWF_PATH_PENCIL
   int path[2] = {IWF_PATH_AUTO, IWF_PATH_AUTO};
+  // eigensolver workspace of iwf_eigensolve / iwf_batch_eigensolve, kept between solves: the
+  // buffers in the order a solve requests them, each reused while large enough
+  struct SolveBuf { void* ptr; size_t bytes; };
+  std::vector<SolveBuf> solve_ws;
 };
 
 namespace iwf {

@@ -50,16 +50,47 @@ bool graphs_enabled() {
 
 template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? IWF_PREC_F64 : IWF_PREC_C64; }
 
+// Device buffers of one solve. With a plan, they come from the plan's workspace: the i-th
+// request of a solve reuses the plan's i-th buffer when it is large enough (a solve of the
+// same shape allocates nothing), else that buffer is replaced. Without a plan (the groups of
+// iwf_batch_solve, whose memory must return before the next group starts) they are
+// allocated here and freed with the arena.
 struct Arena {
-  std::vector<void*> ptrs;
-  ~Arena() { for (void* p : ptrs) cudaFree(p); }
+  iwf_plan* plan = nullptr;
+  size_t next = 0;
+  std::vector<void*> own;
+  explicit Arena(iwf_plan* p = nullptr) : plan(p) {}
+  ~Arena() { for (void* q : own) cudaFree(q); }
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
   template <typename U>
   iwf_status get(U** out, size_t count) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(U));
-    if (e != cudaSuccess) return fail(IWF_ERR_ALLOC, "eigensolver workspace allocation failed");
-    ptrs.push_back(p);
-    *out = reinterpret_cast<U*>(p);
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(U);
+    void* q = nullptr;
+    if (!plan) {
+      if (cudaMalloc(&q, bytes) != cudaSuccess)
+        return fail(IWF_ERR_ALLOC, "eigensolver workspace allocation failed");
+      own.push_back(q);
+      *out = reinterpret_cast<U*>(q);
+      return IWF_OK;
+    }
+    auto& ws = plan->solve_ws;
+    if (next < ws.size() && ws[next].bytes >= bytes) {
+      *out = reinterpret_cast<U*>(ws[next++].ptr);
+      return IWF_OK;
+    }
+    if (next < ws.size()) {
+      cudaFree(ws[next].ptr);
+      ws[next] = {nullptr, 0};
+    } else {
+      ws.push_back({nullptr, 0});
+    }
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(IWF_ERR_ALLOC, "eigensolver workspace allocation failed");
+    }
+    ws[next] = {q, bytes};
+    *out = reinterpret_cast<U*>(ws[next++].ptr);
     return IWF_OK;
   }
 };
@@ -417,13 +448,13 @@ iwf_status solve_problems(iwf_plan* p, const ApplyBatch* ab, const iwf_solve_opt
   const size_t all = (size_t)N * b * np;
   const auto t0 = std::chrono::steady_clock::now();
   double2* X;
+  int* flag;
   IWF_TRY(ar.get(&X, all));
+  IWF_TRY(ar.get(&flag, 1));     // requested either way: the workspace sequence stays fixed
   if (X0) {
     // a non-finite start block is an input error (it would otherwise surface later, or be
     // masked by the orthonormalisation dropping its columns)
-    int* flag;
     int h_flag = 0;
-    IWF_TRY(ar.get(&flag, 1));
     IWF_TRY(any_nonfinite(reinterpret_cast<const double*>(X0), 2 * (long long)all, flag, st));
     IWF_CUDA(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     IWF_CUDA(cudaStreamSynchronize(st));
@@ -521,7 +552,7 @@ iwf_status eigensolve_impl(iwf_plan* p, const iwf_solve_opts* o, const void* X0,
   if (p->pot_kind == 0) return fail(IWF_ERR_ARG, "iwf_eigensolve: no potential set");
   SolveStream ss;
   IWF_TRY(ss.open(st));
-  Arena ar;
+  Arena ar(p);
   Small sm;
   IWF_TRY(alloc_small(ar, sm, 1));
   const double sigma = p->voff_abs - p->vg0 + 1.0;
@@ -542,7 +573,7 @@ iwf_status batch_eigensolve_impl(iwf_plan* p, int nprob, const int* nmodes, cons
   if ((long long)nprob * b > 65535) return fail(IWF_ERR_ARG, "iwf_batch_eigensolve: nprob * block > 65535");
   SolveStream ss;
   IWF_TRY(ss.open(st));
-  Arena ar;
+  Arena ar(p);
   Small sm;
   IWF_TRY(alloc_small(ar, sm, nprob));
   long long stride = 0;

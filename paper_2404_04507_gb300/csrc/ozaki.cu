@@ -141,27 +141,54 @@ __host__ __device__ constexpr int round8(int x) { return (x + 7) & ~7; }
 // The MMAs of one K16 step, for A digits k and runs of B digits l0..l0+n-1 (consecutive levels
 // k + l, whose accumulators sit next to each other): entry = A tile index k - 1, B tile
 // index l0 - 1, first accumulator k + l0 - 2, run length n, and whether the run's
-// accumulators already hold partial sums. plan[0] is the first step of an accumulation
-// (every accumulator fresh), plan[1] any later step. Returns the number of entries of each.
+// accumulators already hold partial sums. The plan of the first step of an accumulation
+// (every accumulator fresh) differs from that of any later step. A run covers at most
+// max_cat B digits (N = n NMMA <= 256). Built at compile time.
 struct MmaStep { uint8_t a, b, acc, n, add; };
 constexpr int kMaxPlan = 24;
-__device__ __forceinline__ int make_plan(MmaStep* out, bool first, int max_cat) {
+struct MmaPlan { MmaStep s[kMaxPlan]; int n; };
+__host__ __device__ constexpr MmaPlan make_plan(bool first, int max_cat) {
+  MmaPlan P{};
   uint32_t started = first ? 0u : 0xFFFFFFFFu;
   int cnt = 0;
   for (int k = 1; k <= kDig; ++k) {
-    const int lmax = min(kDig, kMaxLvl - k);
+    const int lmax = (kDig < kMaxLvl - k) ? kDig : kMaxLvl - k;
     int l = 1;
     while (l <= lmax) {
       const int l0 = l;
       const uint32_t st0 = (started >> (k + l0 - 2)) & 1u;
       while (l <= lmax && l - l0 < max_cat && ((started >> (k + l - 2)) & 1u) == st0) ++l;
       const int n = l - l0;
-      out[cnt++] = MmaStep{(uint8_t)(k - 1), (uint8_t)(l0 - 1), (uint8_t)(k + l0 - 2), (uint8_t)n,
-                           (uint8_t)st0};
+      P.s[cnt].a = (uint8_t)(k - 1);
+      P.s[cnt].b = (uint8_t)(l0 - 1);
+      P.s[cnt].acc = (uint8_t)(k + l0 - 2);
+      P.s[cnt].n = (uint8_t)n;
+      P.s[cnt].add = (uint8_t)st0;
+      ++cnt;
       started |= ((1u << n) - 1u) << (k + l0 - 2);
     }
   }
-  return cnt;
+  P.n = cnt;
+  return P;
+}
+template <int NMMA> constexpr int max_cat() { return 256 / NMMA < kDig ? 256 / NMMA : kDig; }
+static_assert(make_plan(true, 5).n <= kMaxPlan && make_plan(false, 5).n <= kMaxPlan &&
+                  make_plan(true, 8).n <= kMaxPlan && make_plan(false, 8).n <= kMaxPlan,
+              "plan size");
+
+// The MMAs of one K16 step, unrolled at compile time from the plan: A digit tiles every
+// a_unit * 16 bytes from dA, B digit tiles of NMMA rows from dB, accumulators NMMA columns
+// apart from tmem.
+template <int NMMA, bool FIRST, int I = 0>
+__device__ __forceinline__ void issue_plan(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t a_unit) {
+  constexpr MmaPlan P = make_plan(FIRST, max_cat<NMMA>());
+  if constexpr (I < P.n) {
+    constexpr MmaStep m = P.s[I];
+    tc::mma_bf16(tmem + (uint32_t)(m.acc * NMMA), dA + (uint64_t)(m.a * a_unit),
+                 dB + (uint64_t)((m.b * NMMA * tc::kTileRowBytes) >> 4),
+                 tc::idesc_bf16(128, m.n * NMMA, false), m.add != 0);
+    issue_plan<NMMA, FIRST, I + 1>(tmem, dA, dB, a_unit);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -205,6 +232,7 @@ constexpr int kGuard = 4096;             // tail room for the MMAs' reads past t
 constexpr int kNumLvl = kMaxLvl - 1;     // accumulators, levels 2..10
 constexpr int kChunkRows = 512;          // a level sum over 512 rows stays below 2^24 units
 constexpr int kMaxSub = 12;
+static_assert((kStageRows / 8) * (48 + 24) <= kProdWarps * 32, "one staging item per producer thread");
 
 struct SubGram { int a0, na, b0, nb, poff; };
 struct SubList {
@@ -234,7 +262,6 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_per_slot, int S,
                SubList subs, double* partial, int* err) {
   constexpr int kTileB = NMMA * tc::kTileRowBytes;
-  constexpr int kMaxCat = 256 / NMMA < kDig ? 256 / NMMA : kDig;
   const int prob = blockIdx.y, slot = blockIdx.x, sub = blockIdx.z;
   if (bt.active && !bt.active[prob]) return;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -242,8 +269,6 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
   __shared__ __align__(8) unsigned long long accf_bar, acce_bar, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
-  __shared__ MmaStep plan[2][kMaxPlan];
-  __shared__ int plan_n[2];
   const SubGram sg = subs.s[sub];
   const int na = sg.na, nb = sg.nb;
   const GramLayout<NMMA> Lo(na, nb);
@@ -279,8 +304,6 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
     tc::bar_init(tc::smem_u32(&done_bar), 1);
     tc::bar_init_fence();
     abort_flag = 0;
-    plan_n[0] = make_plan(plan[0], true, kMaxCat);
-    plan_n[1] = make_plan(plan[1], false, kMaxCat);
   }
   if (warp == 0) {
     tc::tmem_alloc(tc::smem_u32(&tmem_base), 512);
@@ -294,32 +317,39 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
   volatile int* abort_v = &abort_flag;
 
   if (warp < kProdWarps) {
-    // ---- producers: item = (column, 8-row group) of A or B, 8 rows x (re, im); this thread
-    // owns the same items in every stage, so it only ever reads the staging slots it filled
-    // itself. Staging is [row u][item], so that a warp's reads are consecutive ----
-    // item it: K half h = it & 1, column cc = (it >> 1) % ncols, K16 step t = (it >> 1) / ncols,
-    // so that a warp's tile stores cover whole 256-byte atoms of one step
-    const int tid = threadIdx.x;
+    // ---- producers: item = (column, 8-row group) of A or B, 8 rows x (re, im); thread tid
+    // owns item tid in every stage (items <= 4 (48 + 24) < kProdWarps * 32), so it only ever
+    // reads the staging slots it filled itself. Staging is [row u][item], so that a warp's
+    // reads are consecutive. Item it: K half h = it & 1, column cc = (it >> 1) % ncols, K16
+    // step t = (it >> 1) / ncols, so that a warp's tile stores cover whole 256-byte atoms of
+    // one step ----
+    const int it = threadIdx.x;
     const int ncols = na + nb;
-    const auto grp_of = [&](int it) { return 2 * ((it >> 1) / ncols) + (it & 1); };
-    const auto col_of = [&](int it, bool& isA, int& c) -> const double2* {
-      const int cc = (it >> 1) % ncols;
-      isA = cc < na;
-      c = isA ? cc : cc - na;
-      const int g = isA ? sg.a0 + c : sg.b0 + c;
-      const BlockList& L = isA ? A : B;
-      return reinterpret_cast<const double2*>(L.p[g / L.b]) + poff + (size_t)(g % L.b) * N;
-    };
+    const bool has = it < Lo.items;
+    const int cc = (it >> 1) % ncols;
+    const int grp = 2 * ((it >> 1) / ncols) + (it & 1), t = grp >> 1, h = grp & 1;
+    const bool isA = cc < na;
+    const int c = isA ? cc : cc - na;
+    const int gcol = isA ? sg.a0 + c : sg.b0 + c;
+    const double2* col = nullptr;
+    if (has) {
+      const void* gbase = isA ? A.p[gcol / A.b] : B.p[gcol / B.b];
+      col = reinterpret_cast<const double2*>(gbase) + poff + (size_t)(gcol % (isA ? A.b : B.b)) * N;
+    }
+    const int maxb = has ? (isA ? sexpA[c] : sexpB[c]) : 0;
+    const uint32_t tstride = isA ? (uint32_t)Lo.tileA : (uint32_t)kTileB;
+    // byte offsets of this item's re and im rows inside the step-t digit tiles of a stage
+    const size_t tbase = isA ? (size_t)t * kDig * Lo.tileA
+                             : (size_t)kSteps * kDig * Lo.tileA + (size_t)t * kDig * kTileB;
+    const uint32_t off_re = tile_off(c, h), off_im = tile_off(c + (isA ? na : nb), h);
+    const uint32_t stg = tc::smem_u32(staging) + (uint32_t)it * 16;
     const auto issue = [&](int j) {
-      const int buf = j & 1;
-      const long long r0 = r_begin + (long long)kStageRows * j;
-      for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
-        bool isA; int c;
-        const double2* col = col_of(it, isA, c);
-        const uint32_t dst = tc::smem_u32(staging + (size_t)buf * Lo.staging + (size_t)it * 16);
+      if (has) {
+        const uint32_t dst = stg + (uint32_t)((j & 1) * Lo.staging);
+        const long long r0 = r_begin + (long long)kStageRows * j + 8 * grp;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const long long r = r0 + 8 * grp_of(it) + u;
+          const long long r = r0 + u;
           const bool in = r < r_end;
           cp_async16(dst + (uint32_t)(u * Lo.items * 16), col + (in ? r : r_begin), in ? 16 : 0);
         }
@@ -337,36 +367,24 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
         break;
       }
       if (*abort_v) break;
-      unsigned char* sA = smem + (size_t)st * Lo.stage;           // [kSteps][kDig] A tiles
-      unsigned char* sB = sA + (size_t)kSteps * kDig * Lo.tileA;  // [kSteps][kDig] B tiles
-      for (int it = tid; it < Lo.items; it += kProdWarps * 32) {
-        const int g = grp_of(it), t = g >> 1, h = g & 1;
-        bool isA; int c;
-        col_of(it, isA, c);
-        const double2* sv = reinterpret_cast<const double2*>(staging + (size_t)(j & 1) * Lo.staging) + it;
+      if (has) {
+        const double2* sv =
+            reinterpret_cast<const double2*>(staging + (size_t)(j & 1) * Lo.staging) + it;
         double re[8], im[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) { const double2 v = sv[u * Lo.items]; re[u] = v.x; im[u] = v.y; }
-        if (isA) {
-          unsigned char* tA = sA + (size_t)t * kDig * Lo.tileA;
-          const int maxb = sexpA[c];
-          store_digits8(re, maxb, tA, Lo.tileA, tile_off(c, h));
-          store_digits8(im, maxb, tA, Lo.tileA, tile_off(c + na, h));
-        } else {
-          unsigned char* tB = sB + (size_t)t * kDig * kTileB;
-          const int maxb = sexpB[c];
-          store_digits8(re, maxb, tB, kTileB, tile_off(c, h));
-          store_digits8(im, maxb, tB, kTileB, tile_off(c + nb, h));
-        }
+        unsigned char* tb = smem + (size_t)st * Lo.stage + tbase;
+        store_digits8(re, maxb, tb, tstride, off_re);
+        store_digits8(im, maxb, tb, tstride, off_im);
       }
       tc::fence_async_smem();
       tc::bar_arrive(tc::smem_u32(&full_bar[st]));
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kProdWarps) {
-    // ---- MMA issuer: the precomputed plan of each K16 step ----
+    // ---- MMA issuer: the compile-time plan of each K16 step ----
     if (lane == 0) {
-      const int n0 = plan_n[0], n1 = plan_n[1];
+      const uint32_t a_unit = (uint32_t)Lo.tileA >> 4;
       for (int j = 0; j < nstages && !*abort_v; ++j) {
         const int st = j % S;
         const int chunk = j / kStagesPerChunk;
@@ -387,16 +405,8 @@ gram_tc_kernel(Batch bt, BlockList A, BlockList B, long long N, long long rows_p
         for (int t = 0; t < kSteps; ++t) {
           const uint64_t dA = tc::sdesc(aBase + t * kDig * Lo.tileA);
           const uint64_t dB = tc::sdesc(bBase + t * kDig * kTileB);
-          const int pi = (fresh && t == 0) ? 0 : 1;
-          const int cnt = pi ? n1 : n0;
-          const MmaStep* pl = plan[pi];
-#pragma unroll 4
-          for (int i = 0; i < cnt; ++i) {
-            const MmaStep m = pl[i];
-            tc::mma_bf16(tmem + (uint32_t)(m.acc * NMMA), dA + (uint64_t)((m.a * Lo.tileA) >> 4),
-                         dB + (uint64_t)((m.b * kTileB) >> 4),
-                         tc::idesc_bf16(128, m.n * NMMA, false), m.add != 0);
-          }
+          if (fresh && t == 0) issue_plan<NMMA, true>(tmem, dA, dB, a_unit);
+          else issue_plan<NMMA, false>(tmem, dA, dB, a_unit);
         }
         tc::mma_commit(tc::smem_u32(&empty_bar[st]));
         if (j % kStagesPerChunk == kStagesPerChunk - 1 || j == nstages - 1)
@@ -575,7 +585,6 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
 update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, const double2* C2,
                  int cstride, int q, double2* out1, double2* out2, int nout, int* err) {
   using Cfg = UpdCfg<NMMA>;
-  constexpr int kMaxCat = 256 / NMMA < kDig ? 256 / NMMA : kDig;
   const int prob = blockIdx.y;
   if (bt.active && !bt.active[prob]) return;
   const int o = blockIdx.x % nout, slot = blockIdx.x / nout, nslots = gridDim.x / nout;
@@ -587,8 +596,7 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
   __shared__ int abort_flag;
   __shared__ int rowexp[kRxRing][128];
   __shared__ int colexpB[NMMA];
-  __shared__ MmaStep plan[2][kMaxPlan];
-  __shared__ int plan_n[2];
+  __shared__ const double2* scol[kMaxSmall];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t poff = (size_t)prob * bt.pstride;
   const double2* C = (o == 0 ? C1 : C2) + (size_t)prob * cstride;
@@ -628,9 +636,10 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
     }
     tc::bar_init_fence();
     abort_flag = 0;
-    plan_n[0] = make_plan(plan[0], true, kMaxCat);
-    plan_n[1] = make_plan(plan[1], false, kMaxCat);
   }
+  // the base pointer of every S column (so that no thread indexes the parameter block)
+  for (int c = threadIdx.x; c < m; c += blockDim.x)
+    scol[c] = reinterpret_cast<const double2*>(S.p[c / S.b]) + poff + (size_t)(c % S.b) * N;
   __syncthreads();
   // B row n, K-elements 16 s + 8 h .. + 7 = S columns c = 8 s + 4 h + u (re, im interleaved):
   // row 2j:   Re Y_j = sum_c Re S_c Re C_cj - Im S_c Im C_cj
@@ -665,9 +674,7 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
     // ---- producers: thread (rho, hh) owns row rho of the tile and half of its columns;
     // both halves of a row sit in one warp, so the row's scale is a shuffle away ----
     const int rho = warp * 16 + (lane & 15), hh = lane >> 4;
-    const auto ld = [&](int c, long long r) {
-      return reinterpret_cast<const double2*>(S.p[c / S.b])[poff + (size_t)(c % S.b) * N + r];
-    };
+    const auto ld = [&](int c, long long r) { return scol[c][r]; };
     int j = 0;                                  // slices produced so far (ring position)
     int tcount = 0;
     for (long long t = slot; t < ntiles && !*abort_v; t += nslots, ++tcount) {
@@ -755,16 +762,8 @@ update_tc_kernel(Batch bt, BlockList S, int m, long long N, const double2* C1, c
           tc::fence_after_sync();
           const uint64_t dA = tc::sdesc(tc::smem_u32(ring + (size_t)st * kUpdSliceBytes));
           const uint64_t dB = tc::sdesc(tc::smem_u32(Bt + (size_t)sl * kDig * Cfg::kTileB));
-          const int pi = sl == 0 ? 0 : 1;
-          const int cnt = plan_n[pi];
-          const MmaStep* pl = plan[pi];
-#pragma unroll 4
-          for (int i = 0; i < cnt; ++i) {
-            const MmaStep m = pl[i];
-            tc::mma_bf16(tmem + (uint32_t)(m.acc * NMMA), dA + (uint64_t)((m.a * kTileA) >> 4),
-                         dB + (uint64_t)((m.b * Cfg::kTileB) >> 4),
-                         tc::idesc_bf16(128, m.n * NMMA, false), m.add != 0);
-          }
+          if (sl == 0) issue_plan<NMMA, true>(tmem, dA, dB, (uint32_t)kTileA >> 4);
+          else issue_plan<NMMA, false>(tmem, dA, dB, (uint32_t)kTileA >> 4);
           tc::mma_commit(tc::smem_u32(&empty_bar[st]));
         }
         if (!ok) break;
