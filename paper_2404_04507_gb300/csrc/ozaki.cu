@@ -44,7 +44,8 @@ constexpr int kSmemCap = 227 * 1024 - 2048;  // dynamic shared memory per CTA (2
 // D_k = d_k 2^(-7(k-1)), |d_k| <= 64 (at most 7 significant bits: the top half is bf16).
 // The scaling is an integer add to v's exponent field and the rounding one hardware
 // conversion to a 64-bit integer (measured faster here than a rounded shift of the mantissa in
-// integer arithmetic); the digits then come from two 28-bit halves in 32-bit arithmetic.
+// 64-bit integer arithmetic, with either the tensor-core issue or the slicing as the
+// bottleneck); the digits then come from two 28-bit halves in 32-bit arithmetic.
 // Zeros, denormals and values below 2^(E-56) give zero digits.
 __device__ __forceinline__ void digits8(double v, int maxb, uint32_t (&f)[kDig]) {
   const long long bits = __double_as_longlong(v);
@@ -192,13 +193,19 @@ __device__ __forceinline__ void issue_plan(uint32_t tmem, uint64_t dA, uint64_t 
 }
 
 // ---------------------------------------------------------------------------------------
-// Column scales: exps[c] = largest biased FP64 exponent over the re and im parts of column c
-// (2047 when the column holds an Inf or NaN, 0 for a zero column). exps must start at 0.
-__global__ void colexp_kernel(Batch bt, BlockList A, long long N, int* exps) {
+// Column scales of both Gram operands: exps[c] (c < ma: column c of A) and
+// exps[kMaxSmall + c] (column c of B) = largest biased FP64 exponent over the re and im parts
+// of the column (2047 when it holds an Inf or NaN, 0 for a zero column). With same = 1 (A and
+// B are one block list) only A is read and both slots are written. exps must start at 0.
+__global__ void colexp_kernel(Batch bt, BlockList A, BlockList B, int ma, int same, long long N,
+                              int* exps) {
   const int prob = blockIdx.z, c = blockIdx.y;
   if (bt.active && !bt.active[prob]) return;
-  const double2* col = reinterpret_cast<const double2*>(A.p[c / A.b]) +
-                       (size_t)prob * bt.pstride + (size_t)(c % A.b) * N;
+  const bool isA = c < ma;
+  const int cc = isA ? c : c - ma;
+  const void* base = isA ? A.p[cc / A.b] : B.p[cc / B.b];
+  const double2* col = reinterpret_cast<const double2*>(base) + (size_t)prob * bt.pstride +
+                       (size_t)(cc % (isA ? A.b : B.b)) * N;
   unsigned int m = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -208,7 +215,11 @@ __global__ void colexp_kernel(Batch bt, BlockList A, long long N, int* exps) {
     m = max(m, max((hx >> 20) & 0x7FFu, (hy >> 20) & 0x7FFu));
   }
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(exps + (size_t)prob * 2 * kMaxSmall + c, (int)m);
+  if ((threadIdx.x & 31) == 0 && m) {
+    int* e = exps + (size_t)prob * 2 * kMaxSmall;
+    atomicMax(e + (isA ? cc : kMaxSmall + cc), (int)m);
+    if (same) atomicMax(e + kMaxSmall + cc, (int)m);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -933,14 +944,16 @@ iwf_status launch_update_tc(const Batch& bt, const BlockList& S, int m, long lon
 
 }  // namespace
 
-iwf_status colexp(const Batch& bt, const BlockList& A, long long N, int off, cudaStream_t s) {
-  const int m = A.nb * A.b;
-  int* exps = bt.exps + off;
-  // clear this operand's slots of every problem (fixed capacity 2 * kMaxSmall per problem)
-  IWF_CUDA(cudaMemset2DAsync(exps, sizeof(int) * 2 * kMaxSmall, 0, sizeof(int) * m, bt.nprob, s));
+// Column scales of A and B (one memset of the problems' scale slots, one kernel)
+iwf_status colexp(const Batch& bt, const BlockList& A, const BlockList& B, long long N,
+                  cudaStream_t s) {
+  const int ma = A.nb * A.b, mb = B.nb * B.b;
+  bool same = ma == mb && A.b == B.b;
+  for (int i = 0; same && i < A.nb; ++i) same = A.p[i] == B.p[i];
+  IWF_CUDA(cudaMemsetAsync(bt.exps, 0, sizeof(int) * 2 * kMaxSmall * (size_t)bt.nprob, s));
   const long long blocks = std::max<long long>(1, std::min<long long>(64, (N + 4095) / 4096));
-  colexp_kernel<<<dim3((unsigned)blocks, (unsigned)m, (unsigned)bt.nprob), 256, 0, s>>>(
-      bt, A, N, exps);
+  colexp_kernel<<<dim3((unsigned)blocks, (unsigned)(same ? ma : ma + mb), (unsigned)bt.nprob),
+                  256, 0, s>>>(bt, A, B, ma, same ? 1 : 0, N, bt.exps);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return IWF_OK;
@@ -952,8 +965,7 @@ iwf_status gram_tc(const Batch& bt, const BlockList& A, const BlockList& B, long
   const int ma = A.nb * A.b, mb = B.nb * B.b;
   if (!bt.exps) return fail(IWF_ERR_ARG, "gram_tc: no exponent scratch");
   if (ma > kMaxSmall || mb > kMaxSmall) return fail(IWF_ERR_ARG, "gram_tc: shape");
-  IWF_TRY(colexp(bt, A, N, 0, s));
-  IWF_TRY(colexp(bt, B, N, kMaxSmall, s));
+  IWF_TRY(colexp(bt, A, B, N, s));
   // sub-Grams: A in blocks of 48 columns, B in blocks of 24 (the last ones shorter)
   const int nA = (ma + 47) / 48, nB = (mb + 23) / 24;
   SubList subs{};

@@ -3,12 +3,12 @@ Rayleigh-Ritz step, Sec. 4.1, Alg. 2 in block form) against their plain definiti
 FP64 matrix product, through the C ABI (iwf_gram, iwf_block_update).
 
 Tolerances follow from the arithmetic. The tensor-core engine rounds every value once to a
-49-bit fixed-point integer under its group's power-of-two scale (|error| <= 2^-48 of the
-group's largest magnitude, unbiased) and drops digit pairs below 2^-50 of the scales'
-product; random data then gives errors near 2^-48 |a| |b|. The bounds below, 2^-46 of the
-column-norm product for a Gram entry and 2^-44 of the row-norm times column-norm product for
-an update entry (up to 144 terms), leave a margin of a few bits. The FP64 engine meets the
-same bounds; the double-float engine, whose splits truncate, gets two bits more.
+56-bit fixed-point integer under its group's power-of-two scale (|error| <= 2^-56 of the
+scale 2^E >= the group's largest magnitude) and drops digit pairs below 2^-62 of the scales'
+product; the sums carry fp32 rounding only in levels below 2^-56. The bounds below, 2^-46 of
+the column-norm product for a Gram entry and 2^-44 of the row-norm times column-norm product
+for an update entry (up to 144 terms), hold the FP64 engine too; the double-float engine,
+whose splits truncate, gets two bits more.
 """
 import numpy as np
 import pytest
