@@ -257,7 +257,10 @@ void iwf_plan_trim(iwf_plan* plan);
  * Learned warm start (no counterpart in the paper, whose start vector is e_1; Sec. 4.1):
  * an MLP from a potential's parameters to the lowest eigenvectors on a small "core" window.
  * Dense layers use bfloat16 weights and inputs with float32 accumulation on the tensor
- * cores, GELU between layers, a linear output; float32 master weights and AdamW.
+ * cores (tcgen05.mma, accumulators in tensor memory; K split across CTAs when a layer has
+ * few output tiles), GELU between layers, a linear output; float32 master weights and AdamW.
+ * predict, loss_grad and train synchronise `stream` and return IWF_ERR_TIMEOUT when a GEMM's
+ * bounded wait ran out (the word is then cleared).
  *   dims: nlayers+1 sizes, every one a multiple of 64 (pad the features with zeros).
  *   Output layout per sample: 2*nvec*ncore floats, (v*ncore + i)*2 + {0: re, 1: im}.
  * Loss per sample: |X X^H - Y Y^H|_F^2 / nvec for reference X and prediction Y on the core,

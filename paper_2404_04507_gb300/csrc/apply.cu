@@ -10,6 +10,10 @@
 //                         G_{K,L} -> forward DFT along k_II axes -> roll back; in place;
 //   pass C  (k_I group)   forward DFT along k_I axes -> roll back by lo_j (the scatter T) ->
 //                         add Lambda_k psi_k.
+// A k_II group too large for one shared-memory tile (more than 8192 points, Example 4.3 from
+// L = 20) runs as per-axis passes: inverse DFTs along its slower axes one at a time (KIND 0
+// on a one-axis group), the last axis with the multiply by V as pass B, then the forward DFTs
+// back along the slower axes (KIND 3).
 // Rolls are index permutations inside a pencil and cost no arithmetic. Vectors are processed
 // in chunks sized so that the intermediate block stays resident in the 129 MB L2.
 //
@@ -73,6 +77,10 @@ struct PassArgs {
   int tile_bytes;           // shared-memory bytes of the tile (pass B's V tables follow it)
   int vec_base;             // index of the launch's first vector in the whole block
   const void* ltw[IWF_MAX_N];  // group axes longer than IWF_MAX_LEN: exp(2 pi i j / len)
+  // pass B split into per-axis passes (a k_II group too large for one tile): the group is
+  // k_II axes [ii0, ii0 + ng); the slower k_II axes index the outer range, the faster ones
+  // the inner range above the k_I slice (0 and ng for the unsplit pass B)
+  int ii0;
 };
 
 // Roll offset of axis a for outer tile index o: pencil element k* lives at (k* + off) mod len.
@@ -325,22 +333,42 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
 
   if (KIND == 0) {
     for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, +1, true, false, LONG>(tile, a, ax, o0, s_off);
+  } else if (KIND == 3) {
+    for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, -1, false, true, LONG>(tile, a, ax, o0, s_off);
   } else if (KIND == 1) {
     for (int ax = 0; ax < a.grp.ng; ++ax) run_axis<T, +1, true, false, LONG>(tile, a, ax, o0, s_off);
     // multiply by V(y_l)/N: l_II from the group point, l_I from the inner index. With
     // per-axis tables V = [const + sum over k_I axes] + [sum over k_II axes]; both parts are
     // tabulated once per tile (vI over the C inner indices, vII over the M group points).
+    // (Ot = 1 here: the inner range is above one point.) With a split k_II group the slower
+    // k_II axes come from the outer index o0 and the faster ones from the inner index above
+    // the k_I slice.
+    const int nII = a.g.n - a.g.d, ii1 = a.ii0 + a.grp.ng;
     if (a.pot.kind == 1) {
       T* vII = reinterpret_cast<T*>(smem_raw + a.tile_bytes);
       T* vI = vII + M;
       const long long tbase = (long long)prob * a.pot.tab_stride;
+      T vout = pot_const<T>(a.pot);          // slower k_II axes (outer index, C order)
+      {
+        long long rem = o0;
+        for (int j = a.ii0 - 1; j >= 0; --j) {
+          const int lj = (int)(rem % a.g.lens[a.g.d + j]);
+          rem /= a.g.lens[a.g.d + j];
+          vout += pot_tab<T>(a.pot, tbase + a.pot.tab_off[a.g.d + j] + lj);
+        }
+      }
       for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        T v = pot_const<T>(a.pot);
-        long long rem = c0 + c;              // inner index -> l_I coordinates (C order)
+        T v = vout;
+        long long rem = c0 + c;              // inner index -> l_I, then faster l_II (C order)
         for (int j = a.g.d - 1; j >= 0; --j) {
           const int lj = (int)(rem % a.g.lens[j]);
           rem /= a.g.lens[j];
           v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[j] + lj);
+        }
+        for (int j = nII - 1; j >= ii1; --j) {
+          const int lj = (int)(rem % a.g.lens[a.g.d + j]);
+          rem /= a.g.lens[a.g.d + j];
+          v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[a.g.d + j] + lj);
         }
         vI[c] = v;
       }
@@ -350,7 +378,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
         for (int ax = a.grp.ng - 1; ax >= 0; --ax) {
           const int lj = gr % a.grp.len[ax];
           gr /= a.grp.len[ax];
-          v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[a.g.d + ax] + lj);
+          v += pot_tab<T>(a.pot, tbase + a.pot.tab_off[a.g.d + a.ii0 + ax] + lj);
         }
         vII[g] = v;
       }
@@ -363,7 +391,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
       }
     } else {
       for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const T v = pot_grid<T>(a.pot, (long long)(e >> lc) * a.inner + c0 + (e & (C - 1)));
+        const T v = pot_grid<T>(a.pot, ((long long)o0 * M + (e >> lc)) * a.inner + c0 +
+                                           (e & (C - 1)));
         V2 x = tile[padx(e)];
         x.x *= v; x.y *= v;
         tile[padx(e)] = x;
@@ -931,8 +960,10 @@ iwf_status stop_timer(PassTimer* timer, int kind, cudaStream_t stream) {
   return IWF_OK;
 }
 
+// tkind: the pass (0 A, 1 B, 2 C) whose time the launch counts toward (-1: its own KIND)
 template <typename T, int KIND>
-iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer, int threads) {
+iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* timer, int threads,
+                       int tkind = -1) {
   const size_t elems = (size_t)a.Ot * a.M * a.C;
   const size_t tbytes = ((elems + elems / 32 + 1) * sizeof(typename Vec2<T>::type) + 15) / 16 * 16;
   a.tile_bytes = (int)tbytes;
@@ -944,7 +975,7 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
     if (elems > (size_t)vmin * kLongThreads)
       return fail(IWF_ERR_UNSUPPORTED, "apply: axis group too large for the shared-memory FFT");
   }
-  static bool attr_set[2][3][2] = {};
+  static bool attr_set[2][4][2] = {};
   const int ti = sizeof(T) == 8 ? 0 : 1;
   const int li = vmin > 0 ? 1 : 0;
   auto kern = vmin > 0 ? pass_long_kernel<T, KIND> : pass_kernel<T, KIND>;
@@ -958,7 +989,17 @@ iwf_status launch_pass(PassArgs a, int nvec, cudaStream_t stream, PassTimer* tim
   kern<<<grid, threads, bytes, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
   count_launch();
-  return timer ? stop_timer(timer, KIND, stream) : IWF_OK;
+  return timer ? stop_timer(timer, tkind >= 0 ? tkind : KIND, stream) : IWF_OK;
+}
+
+// Whether pass B's whole k_II group fits one shared-memory tile (else it runs per axis).
+template <typename T>
+bool group_fits(const PassArgs& a) {
+  const size_t el = sizeof(typename Vec2<T>::type);
+  const size_t tbytes = ((size_t)a.M + a.M / 32 + 1) * el + (size_t)(a.M + 1) * sizeof(T);
+  if (tbytes > 200 * 1024) return false;
+  const int vmin = long_group_values(a);
+  return vmin == 0 || (size_t)a.M <= (size_t)vmin * kLongThreads;
 }
 
 // Pencil path: two k_I axes of one length and two k_II axes of one length, each 16 or 32.
@@ -1167,7 +1208,29 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
   }
   for (int j = 0; j < n - d; ++j)
     B.ltw[j] = sizeof(T) == 8 ? (const void*)p->d_ltw64[d + j] : (const void*)p->d_ltw32[d + j];
-  choose_tile<T>(B, tile_kb);
+  B.ii0 = 0;
+  // a k_II group too large for one tile: one pass per k_II axis (slower axes outer, faster
+  // axes and the k_I slice inner)
+  const bool split = !group_fits<T>(B);
+  PassArgs Bs[IWF_MAX_N];
+  if (split) {
+    long long outer = 1;
+    for (int j = 0; j < n - d; ++j) {
+      PassArgs& q = Bs[j];
+      q = B;
+      q.grp.ng = 1;
+      q.grp.len[0] = g.lens[d + j]; q.grp.gs[0] = 1; q.grp.kI[0] = -1; q.grp.Lroll[0] = g.half[d + j];
+      q.ltw[0] = B.ltw[j];
+      q.M = g.lens[d + j];
+      q.outer = outer;
+      q.inner = g.MII / outer / g.lens[d + j] * g.MI;
+      q.ii0 = j;
+      outer *= g.lens[d + j];
+      choose_tile<T>(q, tile_kb);
+    }
+  } else {
+    choose_tile<T>(B, tile_kb);
+  }
 
   PassArgs Cp = A;
   Cp.lam = sizeof(T) == 8 ? (const void*)p->d_lam64 : (const void*)p->d_lam32;
@@ -1196,8 +1259,16 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     A.vec_base = v0; B.vec_base = v0; Cp.vec_base = v0;
     A.in = in; A.out = wk;
     IWF_TRY((launch_pass<T, 0>(A, nv, stream, timer, threads)));
-    B.in = wk; B.out = wk;
-    IWF_TRY((launch_pass<T, 1>(B, nv, stream, timer, threads)));
+    if (split) {
+      const int m = n - d;
+      for (int j = 0; j < m; ++j) { Bs[j].vec_base = v0; Bs[j].in = wk; Bs[j].out = wk; }
+      for (int j = 0; j + 1 < m; ++j) IWF_TRY((launch_pass<T, 0>(Bs[j], nv, stream, timer, threads, 1)));
+      IWF_TRY((launch_pass<T, 1>(Bs[m - 1], nv, stream, timer, threads)));
+      for (int j = m - 2; j >= 0; --j) IWF_TRY((launch_pass<T, 3>(Bs[j], nv, stream, timer, threads, 1)));
+    } else {
+      B.in = wk; B.out = wk;
+      IWF_TRY((launch_pass<T, 1>(B, nv, stream, timer, threads)));
+    }
     Cp.in = wk; Cp.out = out; Cp.psi = in;
     IWF_TRY((launch_pass<T, 2>(Cp, nv, stream, timer, threads)));
   }

@@ -119,8 +119,8 @@ iwf_status plan_create(iwf_plan** out, int d, int n, const double* P, const int*
     g.N *= 2 * h;
     if (j < d) g.MI *= 2 * h; else g.MII *= 2 * h;
   }
-  if (g.MI > IWF_MAX_GROUP || g.MII > IWF_MAX_GROUP)
-    return fail(IWF_ERR_UNSUPPORTED, "iwf_plan_create: (2K)^d or (2L)^(n-d) above 8192");
+  if (g.MI > IWF_MAX_GROUP)
+    return fail(IWF_ERR_UNSUPPORTED, "iwf_plan_create: (2K)^d above 8192");
 
   iwf_plan* p = new (std::nothrow) iwf_plan();
   if (!p) return fail(IWF_ERR_ALLOC, "iwf_plan_create: host allocation failed");

@@ -2,8 +2,8 @@
 // fixed core window, trained with a gauge-invariant subspace loss, and its prediction is
 // embedded into a larger window as the eigensolver's start block.
 //
-// Layers: dense (bfloat16 weights and inputs, float32 accumulation on the tensor cores via
-// mma.sync m16n8k16) with GELU between them and a linear output layer. Master weights and
+// Layers: dense (bfloat16 weights and inputs, float32 accumulation in tensor memory by
+// tcgen05.mma) with GELU between them and a linear output layer. Master weights and
 // the AdamW state are float32. The loss per sample is |X X^H - Y Y^H|_F^2 / nvec, X the
 // reference eigenvectors and Y the prediction on the core (flat layout (v*ncore + i)*2 + re/im).
 #include <cuda_bf16.h>
@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 struct iwf_ws {
   int device = 0;
@@ -40,82 +41,168 @@ struct iwf_ws {
   float* dh = nullptr;
   float* gwork = nullptr;           // max(out x in) float32 GEMM output scratch
   float* lossbuf = nullptr;         // per-sample losses
+  float* gsplit = nullptr;          // split-K partial tiles of the tensor-core GEMMs
+  size_t gsplit_cap = 0;
+  int* d_err = nullptr;             // set when a GEMM's bounded wait ran out
 };
 
 namespace iwf {
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 32, kGemmThreads = 128;
+// ---- dense layers on the tcgen05 tensor cores ---------------------------------------------
+// C (M x N, float32, row-major) = A (M x K) . B (N x K)^T, A and B bfloat16 row-major (both
+// K-major), one 128 x 128 tile of C per CTA accumulated in tensor memory. The K range of a CTA
+// is [z kchunk, (z + 1) kchunk) for blockIdx.z = z; with several splits each writes its partial
+// tile to C + z M N (summed by gemm_reduce). All 128 threads stage 64-deep K slices of A and B
+// into a 4-stage ring with cp.async (rows past M or N and K past the end read as zeros); after
+// its copies land each thread makes them visible to the tensor core and arrives on the stage's
+// mbarrier; thread 0 issues the stage's four K16 MMAs and commits them to the stage's "empty"
+// barrier. Every wait is bounded: one that runs out sets *err and the CTA winds down (its
+// copies drained, its MMAs completed) before it releases tensor memory.
+constexpr int kTM = 128, kTN = 128, kTK = 64, kGStages = 4, kGThreads = 128;
+constexpr int kGTile = kTM * tc::kTileRowBytes;                 // 4 KB: 128 rows x K16
+constexpr int kGStageBytes = 2 * (kTK / 16) * kGTile;           // A and B slices: 32 KB
+constexpr int kGSmem = kGStages * kGStageBytes;
+constexpr long long kGSpin = 1LL << 22;
 
-// C (M x N, float32, row-major) = A (M x K) . B (N x K)^T, A and B bfloat16 row-major.
-// M, N multiples of 64, K a multiple of 32. Warps 2 x 2, each a 32 x 32 tile of 2 x 4 mma.
-__global__ void __launch_bounds__(kGemmThreads)
-gemm_nt_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
-             float* __restrict__ C, int M, int N, int K) {
-  __shared__ __align__(16) __nv_bfloat16 As[kBM][kBK + 8];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kBK + 8];
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int g = lane / 4, t4 = lane % 4;
-  const int wm = (warp / 2) * 32, wn = (warp % 2) * 32;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kBK) {
-    // 64 rows x 32 bf16 = 256 vectors of 16 bytes per operand; 2 per thread
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int e = tid + r * kGemmThreads;
-      const int row = e / 4, col = (e % 4) * 8;
-      *reinterpret_cast<uint4*>(&As[row][col]) =
-          *reinterpret_cast<const uint4*>(&A[(size_t)(m0 + row) * K + k0 + col]);
-      *reinterpret_cast<uint4*>(&Bs[row][col]) =
-          *reinterpret_cast<const uint4*>(&B[(size_t)(n0 + row) * K + k0 + col]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int r = wm + 16 * mi + g;
-        af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t4]);
-        af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t4]);
-        af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t4 + 8]);
-        af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t4 + 8]);
-      }
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int c = wn + 8 * ni + g;
-        bfr[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t4]);
-        bfr[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t4 + 8]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-              "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]),
-                "+f"(acc[mi][ni][3])
-              : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]),
-                "r"(bfr[ni][0]), "r"(bfr[ni][1]));
-    }
-    __syncthreads();
+__device__ __forceinline__ bool g_wait(uint32_t bar, uint32_t parity, bool sleep) {
+  for (long long r = 0; r < kGSpin; ++r) {
+    if (tc::bar_try_wait(bar, parity)) return true;
+    if (sleep) __nanosleep(128);
   }
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni) {
-      const int r = m0 + wm + 16 * mi + g, c = n0 + wn + 8 * ni + 2 * t4;
-      *reinterpret_cast<float2*>(&C[(size_t)r * N + c]) = make_float2(acc[mi][ni][0], acc[mi][ni][1]);
-      *reinterpret_cast<float2*>(&C[(size_t)(r + 8) * N + c]) = make_float2(acc[mi][ni][2], acc[mi][ni][3]);
+  return false;
+}
+
+__device__ __forceinline__ void g_cp16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kGThreads, 1)
+gemm_tc_kernel(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
+               float* __restrict__ C, int M, int N, int K, int kchunk, int* err) {
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  __shared__ __align__(8) unsigned long long full_bar[kGStages], empty_bar[kGStages], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int nst = ke > kb ? (ke - kb + kTK - 1) / kTK : 0;
+  float* Cz = C + (size_t)blockIdx.z * M * N;
+  if (tid == 0) {
+    for (int s = 0; s < kGStages; ++s) {
+      tc::bar_init(tc::smem_u32(&full_bar[s]), kGThreads);
+      tc::bar_init(tc::smem_u32(&empty_bar[s]), 1);
     }
+    tc::bar_init(tc::smem_u32(&done_bar), 1);
+    tc::bar_init_fence();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(&tmem_base), 128);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort_v = &abort_flag;
+  const uint32_t base = tc::smem_u32(gsm);
+
+  // stage j: 2 operands x 128 rows x 8 chunks of 16 bytes (K16 step t = chunk / 2, half
+  // h = chunk % 2); thread tid copies chunks tid + 128 i, i < 16
+  const auto load = [&](int j) {
+    const uint32_t sb = base + (uint32_t)((j % kGStages) * kGStageBytes);
+    const int k0 = kb + j * kTK;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int e = tid + kGThreads * i;            // 0 .. 2047
+      const int op = e >> 10, row = (e >> 3) & 127, ch = e & 7;
+      const int t = ch >> 1, h = ch & 1;
+      const int k = k0 + 8 * ch;
+      const int grow = (op == 0 ? m0 : n0) + row;
+      const bool in = grow < (op == 0 ? M : N) && k < ke;
+      const __nv_bfloat16* src = (op == 0 ? A : B) + (in ? (size_t)grow * K + k : 0);
+      const uint32_t dst = sb + (uint32_t)(op * (kGStageBytes / 2) + t * kGTile) +
+                           tc::tile_off(row, h);
+      g_cp16(dst, src, in ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  for (int j = 0; j < kGStages - 1; ++j) {
+    if (j < nst) load(j);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  const uint32_t idesc = tc::idesc_bf16(kTM, kTN, false);
+  for (int j = 0; j < nst && !*abort_v; ++j) {
+    // refill the slot of stage j - 1 with stage j + kGStages - 1 once its MMAs are done
+    const int jn = j + kGStages - 1;
+    if (jn < nst) {
+      if (j >= 1 && !g_wait(tc::smem_u32(&empty_bar[jn % kGStages]),
+                            (uint32_t)(((jn / kGStages) - 1) & 1), false)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      load(jn);
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group %0;" ::"n"(kGStages - 1) : "memory");
+    tc::fence_async_smem();
+    tc::bar_arrive(tc::smem_u32(&full_bar[j % kGStages]));
+    if (tid == 0) {
+      if (!g_wait(tc::smem_u32(&full_bar[j % kGStages]), (uint32_t)((j / kGStages) & 1), false)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sb = base + (uint32_t)((j % kGStages) * kGStageBytes);
+#pragma unroll
+      for (int t = 0; t < kTK / 16; ++t)
+        tc::mma_bf16(tmem, tc::sdesc(sb + t * kGTile), tc::sdesc(sb + kGStageBytes / 2 + t * kGTile),
+                     idesc, j > 0 || t > 0);
+      tc::mma_commit(tc::smem_u32(&empty_bar[j % kGStages]));
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (tid == 0) tc::mma_commit(tc::smem_u32(&done_bar));   // every MMA issued so far
+  const bool ok = g_wait(tc::smem_u32(&done_bar), 0, true) && !*abort_v;
+  tc::fence_after_sync();
+  if (ok) {
+    // row m0 + 32 warp + lane of the tile sits in tensor-memory lane 32 warp + lane
+    const int row = m0 + 32 * warp + lane;
+#pragma unroll 4
+    for (int g = 0; g < kTN / 8; ++g) {
+      float v[8];
+      tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(8 * g), v);
+      tc::tmem_wait_ld();
+      const int col = n0 + 8 * g;
+      if (row < M && col < N) {
+        float4* dst = reinterpret_cast<float4*>(Cz + (size_t)row * N + col);
+        dst[0] = make_float4(nst ? v[0] : 0.f, nst ? v[1] : 0.f, nst ? v[2] : 0.f, nst ? v[3] : 0.f);
+        dst[1] = make_float4(nst ? v[4] : 0.f, nst ? v[5] : 0.f, nst ? v[6] : 0.f, nst ? v[7] : 0.f);
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+// C[i] = sum over the splits of P[z][i]
+__global__ void gemm_reduce(const float* P, float* C, long long count, int splits) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += P[(size_t)z * count + i];
+    C[i] = s;
+  }
 }
 
 // out (C x R) = in (R x C)^T, bfloat16, through a 32 x 33 shared tile.
@@ -316,12 +403,46 @@ __global__ void phase_kernel(Geom g, const int* lo, const double* phases, int np
 
 int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8 * 152)); }
 
-iwf_status gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N, int K,
-                cudaStream_t s) {
-  if (M % kBM || N % kBN || K % kBK) return fail(IWF_ERR_ARG, "gemm: shape not a tile multiple");
-  gemm_nt_bf16<<<dim3(N / kBN, M / kBM), kGemmThreads, 0, s>>>(A, B, C, M, N, K);
+template <typename U> iwf_status dalloc(U** p, size_t n);
+
+// C = A B^T on the tensor cores. A grid of fewer tiles than SMs with a long K splits K across
+// CTAs (partials in w->gsplit, then summed).
+iwf_status gemm(iwf_ws* w, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N,
+                int K, cudaStream_t s) {
+  if (M % 64 || N % 64 || K % 32) return fail(IWF_ERR_ARG, "gemm: shape not a tile multiple");
+  static bool attr[64] = {};
+  int dev = 0;
+  IWF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    IWF_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
+    attr[dev] = true;
+  }
+  const int tm = (M + kTM - 1) / kTM, tn = (N + kTN - 1) / kTN;
+  int splits = 1;
+  if (tm * tn < 152 && K >= 2 * 512) splits = std::min((152 + tm * tn - 1) / (tm * tn), K / 512);
+  const int kchunk = ((K + splits - 1) / splits + kTK - 1) / kTK * kTK;
+  splits = (K + kchunk - 1) / kchunk;
+  float* out = C;
+  if (splits > 1) {
+    const size_t need = (size_t)splits * M * N;
+    if (need > w->gsplit_cap) {
+      cudaFree(w->gsplit);
+      w->gsplit = nullptr;
+      w->gsplit_cap = 0;
+      IWF_TRY(dalloc(&w->gsplit, need));
+      w->gsplit_cap = need;
+    }
+    out = w->gsplit;
+  }
+  gemm_tc_kernel<<<dim3(tn, tm, splits), kGThreads, kGSmem, s>>>(A, B, out, M, N, K, kchunk, w->d_err);
   IWF_CUDA(cudaGetLastError());
   count_launch();
+  if (splits > 1) {
+    const long long cnt = (long long)M * N;
+    gemm_reduce<<<(int)std::min<long long>((cnt + 255) / 256, 4 * 152), 256, 0, s>>>(out, C, cnt, splits);
+    IWF_CUDA(cudaGetLastError());
+    count_launch();
+  }
   return IWF_OK;
 }
 
@@ -362,6 +483,19 @@ iwf_status ensure_batch(iwf_ws* w, int B) {
   return IWF_OK;
 }
 
+// The GEMMs' device error word, read at a synchronisation point of `s` (and cleared).
+iwf_status check_ws_err(iwf_ws* w, cudaStream_t s) {
+  int h = 0;
+  IWF_CUDA(cudaMemcpyAsync(&h, w->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  IWF_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    IWF_CUDA(cudaMemsetAsync(w->d_err, 0, sizeof(int), s));
+    IWF_CUDA(cudaStreamSynchronize(s));
+    return fail(IWF_ERR_TIMEOUT, "warm start: a tensor-core GEMM gave up waiting");
+  }
+  return IWF_OK;
+}
+
 // Forward pass on B samples of features (device float32 B x dims[0]); output (B x dims[nl]).
 iwf_status forward(iwf_ws* w, int B, const float* feat, float* out, cudaStream_t s) {
   IWF_TRY(ensure_batch(w, B));
@@ -370,7 +504,7 @@ iwf_status forward(iwf_ws* w, int B, const float* feat, float* out, cudaStream_t
   count_launch();
   for (int l = 0; l < w->nl; ++l) {
     const int in = w->dims[l], o = w->dims[l + 1];
-    IWF_TRY(gemm(w->hbf[l], w->wbf + w->woff[l], w->gwork, B, o, in, s));
+    IWF_TRY(gemm(w, w->hbf[l], w->wbf + w->woff[l], w->gwork, B, o, in, s));
     const bool last = l + 1 == w->nl;
     bias_act<<<blocks_for((long long)B * o), 256, 0, s>>>(w->gwork, w->params + w->boff[l], w->z[l],
                                                           last ? nullptr : w->hbf[l + 1],
@@ -398,13 +532,13 @@ iwf_status loss_grad(iwf_ws* w, int B, const float* feat, const float* target, i
     count_launch();
     IWF_TRY(transpose(w->dzbf, w->dzt, B, o, s));
     IWF_TRY(transpose(w->hbf[l], w->ht, B, in, s));
-    IWF_TRY(gemm(w->dzt, w->ht, w->grads + w->woff[l], o, in, B, s));
+    IWF_TRY(gemm(w, w->dzt, w->ht, w->grads + w->woff[l], o, in, B, s));
     colsum<<<(o + 255) / 256, 256, 0, s>>>(w->dz, w->grads + w->boff[l], B, o);
     count_launch();
     if (l > 0) {
       // dh = dz W  (B x in) = dz . (W^T)^T ; then dz_{l-1} = dh * gelu'(z_{l-1})
       IWF_TRY(transpose(w->wbf + w->woff[l], w->wtbf, o, in, s));
-      IWF_TRY(gemm(w->dzbf, w->wtbf, w->dh, B, in, o, s));
+      IWF_TRY(gemm(w, w->dzbf, w->wtbf, w->dh, B, in, o, s));
       act_back<<<blocks_for((long long)B * in), 256, 0, s>>>(w->dh, w->z[l - 1], w->dz, (long long)B * in);
       count_launch();
     }
@@ -460,7 +594,9 @@ iwf_status iwf_ws_create(iwf_ws** out, int nlayers, const int* dims, unsigned lo
   if (st == IWF_OK) st = dalloc(&w->wbf, off);
   if (st == IWF_OK) st = dalloc(&w->wtbf, maxw);
   if (st == IWF_OK) st = dalloc(&d_isw, off);
-  if (st != IWF_OK) { iwf_ws_destroy(w); return st; }
+  if (st == IWF_OK) st = dalloc(&w->d_err, 1);
+  if (st != IWF_OK) { cudaFree(d_isw); iwf_ws_destroy(w); return st; }
+  cudaMemset(w->d_err, 0, sizeof(int));
   cudaMemcpy(w->params, h.data(), off * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(d_isw, isw.data(), off, cudaMemcpyHostToDevice);
   cudaMemset(w->m, 0, off * sizeof(float));
@@ -480,7 +616,8 @@ void iwf_ws_destroy(iwf_ws* w) {
   for (int l = 0; l <= w->nl; ++l) { cudaFree(w->hbf[l]); cudaFree(w->z[l]); }
   cudaFree(w->params); cudaFree(w->grads); cudaFree(w->m); cudaFree(w->v); cudaFree(w->wbf);
   cudaFree(w->wtbf); cudaFree(w->dz); cudaFree(w->dzbf); cudaFree(w->dzt); cudaFree(w->ht);
-  cudaFree(w->dh); cudaFree(w->gwork); cudaFree(w->lossbuf);
+  cudaFree(w->dh); cudaFree(w->gwork); cudaFree(w->lossbuf); cudaFree(w->gsplit);
+  cudaFree(w->d_err);
   delete w;
 }
 
@@ -511,7 +648,8 @@ iwf_status iwf_ws_predict(iwf_ws* w, int nsamples, const float* feat, float* out
   if (!w || !feat || !out || nsamples < 0) return fail(IWF_ERR_ARG, "iwf_ws_predict: bad arguments");
   if (nsamples % 64) return fail(IWF_ERR_ARG, "iwf_ws_predict: nsamples must be a multiple of 64");
   DeviceGuard guard(w->device);
-  return forward(w, nsamples, feat, out, (cudaStream_t)stream);
+  IWF_TRY(forward(w, nsamples, feat, out, (cudaStream_t)stream));
+  return check_ws_err(w, (cudaStream_t)stream);
 }
 
 iwf_status iwf_ws_loss_grad(iwf_ws* w, int nsamples, const float* feat, const float* target,
@@ -532,6 +670,7 @@ iwf_status iwf_ws_loss_grad(iwf_ws* w, int nsamples, const float* feat, const fl
     double t = 0;
     for (float v : l) t += v;
     if (loss) *loss = (float)t;
+    if (st == IWF_OK) st = check_ws_err(w, s);
   }
   cudaFree(y);
   return st;
@@ -587,6 +726,7 @@ iwf_status iwf_ws_train(iwf_ws* w, int nsamples, const float* feat, const float*
       count_launch();
       if (cudaStreamSynchronize(s) != cudaSuccess) st = fail(IWF_ERR_CUDA, "iwf_ws_train step");
     }
+    if (st == IWF_OK) st = check_ws_err(w, s);
     if (st == IWF_OK && loss_hist) {
       if (cudaMemcpy(hl.data(), losses, hl.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
         st = fail(IWF_ERR_CUDA, "loss readback");

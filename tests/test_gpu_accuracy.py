@@ -4,7 +4,7 @@ Ground states come from iwf_eigensolve (FP64, residual 1e-10), fields from iwf_e
 the observation grid, iwf_field_normalize and iwf_field_distance (paper_2404_04507_gb300.
 accuracy). E_v compares eigenvalues with a large-window reference: PM and IWFPM on the
 windows of Table 2 (Example 4.1, Case 1), Table 4 (Example 4.1, Case 2) and Table 5
-(Example 4.2, case I).
+(Example 4.2, case I); for Table 9 (Example 4.3) the difference of two printed rows.
 
 References here are cheaper than the paper's yet equivalent to the printed digits:
 Example 4.1 uses IWFPM K = 5, L = 96 instead of PM K = 640, L = 1024 (by Table 2 the
@@ -102,3 +102,26 @@ def test_grid_and_direct_fields_agree(acc):
     for ra, rb in zip(a, b):
         assert ra["E0"] == rb["E0"]
         assert abs(ra["E_f"] - rb["E_f"]) <= 1e-12
+
+
+def test_table9_example43_eigenvalue_differences(acc):
+    # Example 4.3, case I (beta = pi), IWFPM K = 5: L = 10 (8.0e6 DOF) and L = 20 (6.4e7 DOF,
+    # where the k_II group of 40^3 points runs as per-axis passes). The paper's reference
+    # (L = 40, 5.1e8 DOF) is not run here; E0(10) - E0(20) = E0*(E_v(10) - E_v(20)), so the
+    # relative difference of the two ground-state energies must equal the difference of the
+    # printed E_v cells (up to a factor 1 + E_v(20) and the three printed digits: 2 %).
+    import math
+    from paper_2404_04507_gb300 import workloads as W
+    printed = {int(L): float(ev) for case, L, ev in read_golden("table9_ex43_errors.txt")
+               if case == "I"}
+    E = {}
+    for L in (10, 20):
+        r = acc.ground_state(W.example_43(math.pi, 5, L), tol=1e-8, precision="c64", block=1,
+                             maxit=3000)
+        assert r["converged"] == 1, r
+        E[L] = r["E0"]
+        r["plan"].close()
+    want = printed[10] - printed[20]
+    got = (E[10] - E[20]) / E[20]
+    assert abs(got - want) <= 0.02 * want, (got, want, E)
+

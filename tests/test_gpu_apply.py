@@ -352,6 +352,36 @@ def test_long_axes_match_oracle(iwf, name, prec):
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
 
 
+# k_II groups above 8192 points (one shared-memory tile): pass B runs as one pass per k_II
+# axis, the multiply by V in the last one (Example 4.3 from L = 20 needs this)
+SPLIT = {
+    "three_axes_24": W.Problem("s3", np.array([[1.0, 2.0 ** 0.5, 3.0 ** 0.5, 5.0 ** 0.5]]),
+                               (2,), (12, 12, 12), *W.cosine_modes(4, 1.5)),   # 4 x 24^3
+    "long_axes": W.Problem("sl", np.array([[1.0, 2.0 ** 0.5, 3.0 ** 0.5]]), (3,), (64, 40),
+                           *W.cosine_modes(3, 0.7)),                          # 6 x 128 x 80
+    "grid_potential": W.Problem("sg", W.random_P(1, 4, seed=3), (2,), (12, 12, 12),
+                                *W.random_modes(4, 6, 2, seed=7)),             # full-grid V
+    "ex43_K2_L12": W.example_43(math.pi, K=2, L=12),                          # 4^3 x 24^3
+}
+
+
+@pytest.mark.parametrize("name", list(SPLIT))
+@pytest.mark.parametrize("prec", ["f64", "c64"])
+def test_split_k2_group_matches_oracle(iwf, name, prec):
+    pb = SPLIT[name]
+    plan = _plan(iwf, pb)
+    win, Vg = _oracle(pb)
+    assert int(np.prod([2 * l for l in pb.L])) > 8192
+    assert np.array_equal(plan.window().astype(np.int64), win.k)
+    X = W.random_block(win.N, 2, seed=21)
+    dtype = torch.complex128 if prec == "f64" else torch.complex64
+    got = _gpu_apply(plan, X.astype(np.complex64) if prec == "c64" else X, dtype)
+    want = O.apply_stencil(win, Vg, X.astype(np.complex64).astype(np.complex128)
+                           if prec == "c64" else X)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
 @pytest.mark.parametrize("prec", ["f64", "c64"])
 def test_longest_axis_full_size(iwf, prec):
     # 2L = 8192 (L = 4096, the paper's largest 1D window): one k_II group of 8192 points, the

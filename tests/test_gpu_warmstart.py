@@ -49,6 +49,27 @@ def test_gradients_match_oracle(mods):
     assert np.max(np.abs(y - yref)) <= 1e-3 * np.max(np.abs(yref))
 
 
+def test_gradients_match_oracle_long_k_split(mods):
+    # the output layer's input gradient contracts over 4096 outputs with only two 128-column
+    # tiles: the tensor-core GEMM splits K across CTAs and sums the partial tiles
+    _, ws = mods
+    dims, nvec, ncore, B = [64, 256, 4096], 2, 1024, 64
+    net = ws.WarmStart(dims, seed=5)
+    rng = np.random.default_rng(1)
+    flat = mlp.bf16_round(net.get_params()).astype(np.float32)
+    net.set_params(flat)
+    feats = mlp.bf16_round(rng.standard_normal((B, dims[0]))).astype(np.float32)
+    X = rng.standard_normal((B, dims[-1])).astype(np.float32) * 0.05
+    loss, g = net.loss_grad(feats, X, nvec, ncore)
+    lref, gref = mlp.loss_and_grad(flat.astype(np.float64), dims, feats.astype(np.float64),
+                                   X.astype(np.float64), nvec, ncore, bf16=True)
+    assert abs(loss - lref) <= 1e-3 * abs(lref)
+    assert np.linalg.norm(g - gref) <= 2e-2 * np.linalg.norm(gref)
+    # the first layer's weights get their gradient through the split-K product
+    n0 = dims[0] * dims[1]
+    assert np.linalg.norm(g[:n0] - gref[:n0]) <= 2e-2 * np.linalg.norm(gref[:n0])
+
+
 def _core_dataset(iwf, ws, n, seed, K, nev, block):
     # eigenvectors of the sweep's problems on the core window, with the phases removed by
     # the exact diagonal unitary (targets of the phase-free network)
