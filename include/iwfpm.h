@@ -67,9 +67,11 @@ const char* iwf_last_error(void);
  *          PM: the box [-K,K)^d x [-L,L)^{n-d}.
  *   opts   host, may be NULL (IWFPM, exact shift, device 0).
  * Supported: every axis length 2K_j, 2L_j in [2, 32], or in (32, 8192] with no prime factor
- * above 7 (e.g. 40, 120, 1280, 8192); (2K)^d and (2L)^{n-d} at most 8192 each. Axis groups
- * with an axis above 32 run a shared-memory FFT instead of the register codelets; a group
- * holding more than 16 x 512 points per radix stage gives IWF_ERR_UNSUPPORTED at the apply.
+ * above 7 (e.g. 40, 120, 1280, 8192); (2K)^d at most 8192. Axis groups with an axis above 32
+ * run a shared-memory FFT instead of the register codelets. A k_II group too large for one
+ * shared-memory tile ((2L)^{n-d} above 8192 points, or above 16 x 512 points per radix
+ * stage of its FFT) runs as one pass per k_II axis; a k_I group that large gives
+ * IWF_ERR_UNSUPPORTED at the apply.
  * The window, its slice bounds and Lambda = 1/2 |P k|^2 (Eq. discrete_Lambda)
  * are built on the device; the call synchronises the device.
  * Errors: IWF_ERR_ARG, IWF_ERR_SINGULAR_PI, IWF_ERR_UNSUPPORTED, IWF_ERR_WINDOW_TIE,
