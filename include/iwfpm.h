@@ -100,6 +100,24 @@ iwf_status iwf_window(const iwf_plan* plan, int* k);
 iwf_status iwf_kinetic(const iwf_plan* plan, double* lam);
 
 /*
+ * Extent of the concentrated coefficients of a vector on this window (the "concentrated
+ * area" of the Fourier coefficients, Sec. 4.2, Example 4.1): need[j] is the smallest half-
+ * width K'_j (j < d) or L'_j (j >= d) of a window with this plan's centring that contains
+ * every position with |coef_k| >= threshold. For a k_I axis a position at offset o in its
+ * slice (o = k_I,j - lo_j in [0, 2K_j)) needs max(K_j - o, o - K_j + 1); for a k_II axis
+ * the coordinate k_II,j needs max(-k_II,j, k_II,j + 1). need[j] = K_j (or L_j) means the
+ * concentrated coefficients reach the window's edge along axis j; 0 that no position
+ * passes the threshold. Used to size windows automatically from the decay of a solution.
+ *   coef       device, N complex doubles (window order), 16-byte aligned.
+ *   threshold  absolute magnitude, finite and >= 0.
+ *   need       host, n ints.
+ * Synchronises `stream`. Errors: IWF_ERR_ARG, IWF_ERR_CUDA. Library extension (the paper
+ * reads the concentrated area off its figures).
+ */
+iwf_status iwf_coef_extent(const iwf_plan* plan, const void* coef, double threshold, int* need,
+                           void* stream);
+
+/*
  * Set the lifted potential V(y) = sum_m c_m exp(i m.y) (Sec. 4.1, V sampled on G_{K,L}).
  *   nmodes >= 0; m host nmodes*n ints (row per mode); re, im host nmodes doubles.
  * V must be real: every mode m != 0 must come with -m and the conjugate coefficient

@@ -283,6 +283,22 @@ class Plan:
         return {"threads": out[0], "tile_kb": out[1], "chunk_mb": out[2],
                 "path": names[out[3]]}
 
+    def coef_extent(self, coef, threshold, stream=None):
+        """iwf_coef_extent: per axis, the smallest half-width (K'_j, then L'_j) of a window
+        with this plan's centring that holds every coefficient with |c_k| >= threshold
+        (coef: a complex128 CUDA tensor of N values in window order)."""
+        torch = _torch()
+        if not isinstance(coef, torch.Tensor) or not coef.is_cuda or coef.dtype != torch.complex128:
+            raise TypeError("coef must be a complex128 CUDA tensor")
+        c = coef.contiguous()
+        if c.numel() != self.N:
+            raise ValueError("coef must hold N values")
+        need = (C.c_int * self.n)()
+        self._c.check(self._c.iwf_coef_extent(self.handle, C.c_void_p(c.data_ptr()),
+                                              float(threshold), need, self._stream(stream)),
+                      "iwf_coef_extent")
+        return np.array(list(need), dtype=np.int64)
+
     def trim(self):
         """iwf_plan_trim: free the eigensolver workspace kept on the plan between solves."""
         self._c.iwf_plan_trim(self.handle)

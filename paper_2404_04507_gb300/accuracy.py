@@ -86,6 +86,9 @@ def study(windows, reference, d: int, tol: float = 1e-10, precision: str = "f64"
     grid = W.grid_descriptor(d, grid_rows) if (fields and use_grid and d == 2) else None
     ref = ground_state(reference, tol, precision, block=block, maxit=maxit)
     u_ref, i_ref = observe(ref, x, grid=grid) if fields else (None, None)
+    ref["plan"].trim()                    # its eigensolver workspace (large references)
+    if not fields:
+        ref.pop("coef")
     yield {"name": reference.name, "method": reference.method, "K": list(reference.K),
            "L": list(reference.L), "dof": ref["dof"], "E0": ref["E0"], "iters": ref["iters"],
            "resid": ref["resid"], "converged": ref["converged"], "seconds": ref["seconds"],
@@ -96,10 +99,65 @@ def study(windows, reference, d: int, tol: float = 1e-10, precision: str = "f64"
         if fields:
             u, _ = observe(gs, x, at=i_ref, grid=grid)
             ef = float(gs["plan"].field_distance(u, u_ref).item())
+        gs["plan"].close()
         yield {"name": pb.name, "method": pb.method, "K": list(pb.K), "L": list(pb.L),
                "dof": gs["dof"], "E0": gs["E0"], "iters": gs["iters"], "resid": gs["resid"],
                "seconds": gs["seconds"], "converged": gs["converged"],
                "E_v": abs(gs["E0"] - ref["E0"]) / abs(ref["E0"]), "E_f": ef}
+
+
+def _axis_ok(length: int) -> bool:
+    """An axis length the apply supports: up to 32, or up to 8192 with prime factors <= 7."""
+    if length <= 32:
+        return True
+    if length > 8192:
+        return False
+    for f in (2, 3, 5, 7):
+        while length % f == 0:
+            length //= f
+    return length == 1
+
+
+def _next_size(h: int) -> int:
+    while not _axis_ok(2 * h):
+        h += 1
+    return h
+
+
+def autosize(make, K0, L0, rel: float = 1e-8, margin: int = 1, grow: float = 1.25,
+             tol: float = 1e-10, precision: str = "f64", block: int = 16, max_rounds: int = 10):
+    """Window sizing from the decay of the ground state (the concentrated area of the
+    Fourier coefficients, Sec. 4.2): solve on (K, L), find per axis the half-width that holds
+    every coefficient above rel * max |c_k| (iwf_coef_extent), and enlarge each axis whose
+    concentrated coefficients come within `margin` of the window's edge (to the larger of
+    that half-width + margin + 1 and grow x the current one, rounded up to a supported axis
+    length); stop when every axis keeps the margin. make(K, L) returns the Problem for
+    per-axis tuples K, L. Returns one dict per round; the last one is the sized window, with
+    `tight` = the half-widths + margin (a window that would still hold the concentrated
+    area)."""
+    K, L = tuple(int(v) for v in K0), tuple(int(v) for v in L0)
+    rounds = []
+    for _ in range(max_rounds):
+        pb = make(K, L)
+        gs = ground_state(pb, tol, precision, block=block, maxit=5000)
+        c = gs["coef"]
+        amax = float(c.abs().max().item())
+        need = gs["plan"].coef_extent(c, rel * amax)
+        gs["plan"].close()
+        d = len(K)
+        nK, nL = [int(v) for v in need[:d]], [int(v) for v in need[d:]]
+        fits = all(a + margin <= b for a, b in zip(nK + nL, list(K) + list(L)))
+        rounds.append({"K": list(K), "L": list(L), "dof": gs["dof"], "E0": gs["E0"],
+                       "iters": gs["iters"], "converged": gs["converged"],
+                       "seconds": gs["seconds"], "need_K": nK, "need_L": nL, "fits": fits,
+                       "tight": {"K": [a + margin for a in nK], "L": [a + margin for a in nL]}})
+        if fits:
+            break
+        K = tuple(h if a + margin <= h else _next_size(max(a + margin + 1, math.ceil(grow * h)))
+                  for a, h in zip(nK, K))
+        L = tuple(h if a + margin <= h else _next_size(max(a + margin + 1, math.ceil(grow * h)))
+                  for a, h in zip(nL, L))
+    return rounds
 
 
 # ---- the paper's studies (Sec. 4.2) ----

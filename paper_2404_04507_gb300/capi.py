@@ -58,6 +58,7 @@ _PROTOS = {
     "iwf_plan_create": (_i, [C.POINTER(_vp), _i, _i, C.POINTER(C.c_double), C.POINTER(_i),
                              C.POINTER(_i), C.POINTER(iwf_plan_opts)]),
     "iwf_plan_destroy": (None, [_vp]),
+    "iwf_coef_extent": (_i, [_vp, _vp, C.c_double, C.POINTER(C.c_int), _vp]),
     "iwf_plan_trim": (None, [_vp]),
     "iwf_plan_size": (_i, [_vp, C.POINTER(_ll)]),
     "iwf_plan_lens": (_i, [_vp, C.POINTER(_i)]),

@@ -217,6 +217,12 @@ iwf_status iwf_window(const iwf_plan* p, int* k) {
   return export_window(p, k);
 }
 
+iwf_status iwf_coef_extent(const iwf_plan* p, const void* coef, double threshold, int* need,
+                           void* stream) {
+  clear_error();
+  return coef_extent(p, coef, threshold, need, (cudaStream_t)stream);
+}
+
 iwf_status iwf_kinetic(const iwf_plan* p, double* lam) {
   if (!p || !lam) return fail(IWF_ERR_ARG, "iwf_kinetic: NULL argument");
   DeviceGuard guard(p->device);

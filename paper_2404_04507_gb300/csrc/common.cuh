@@ -228,6 +228,8 @@ void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties
 iwf_status export_window(const iwf_plan* p, int* k_host);
+iwf_status coef_extent(const iwf_plan* p, const void* coef, double threshold, int* need,
+                       cudaStream_t s);
 iwf_status build_potential(iwf_plan* p, int nmodes, const int* m, const double* re,
                            const double* im);
 // Potential summaries used by the preconditioner (Eq. precond): Re Vg_0, sum |Vg_m|,

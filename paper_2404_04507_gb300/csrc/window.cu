@@ -8,6 +8,7 @@
 // k_j = lo_j + t_j, which is the inverse of the index-shift map rho (Eqs. inverse1-3).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "common.cuh"
@@ -410,6 +411,70 @@ iwf_status potential_tables(const iwf_plan* p, int nmodes, const int* m, const d
   IWF_CUDA(cudaGetLastError());
   IWF_CUDA(cudaStreamSynchronize(s));
   return IWF_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Extent of the concentrated coefficients (the "concentrated area" of Sec. 4.2): for every
+// axis the smallest half-width of a window with this plan's centring that holds every point
+// with |c_k|^2 >= thr2. In window order a point's k_I offset o_j = k_I,j - lo_j lies in
+// [0, 2K_j) and needs half-width max(K_j - o_j, o_j - K_j + 1); its k_II coordinate t_j - L_j
+// (digit t_j in [0, 2L_j)) needs max(L_j - t_j, t_j - L_j + 1). Maxima over points by warp
+// shuffles and one atomicMax per warp and axis; need[] must start at 0.
+namespace {
+__global__ void coef_extent_kernel(Geom g, const double2* c, double thr2, int* need) {
+  int loc[IWF_MAX_N];
+#pragma unroll
+  for (int j = 0; j < IWF_MAX_N; ++j) loc[j] = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = c[i];
+    if (!(fma(v.x, v.x, v.y * v.y) >= thr2)) continue;
+    long long rem = i % g.MI;                   // in-slice index: k_I offsets, last axis fastest
+    for (int j = g.d - 1; j >= 0; --j) {
+      const int o = (int)(rem % g.lens[j]);
+      rem /= g.lens[j];
+      loc[j] = max(loc[j], max(g.half[j] - o, o - g.half[j] + 1));
+    }
+    rem = i / g.MI;                             // slice index: k_II digits, last axis fastest
+    for (int j = g.n - 1; j >= g.d; --j) {
+      const int t = (int)(rem % g.lens[j]);
+      rem /= g.lens[j];
+      loc[j] = max(loc[j], max(g.half[j] - t, t - g.half[j] + 1));
+    }
+  }
+  for (int j = 0; j < g.n; ++j) {
+    int m = loc[j];
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(need + j, m);
+  }
+}
+}  // namespace
+
+iwf_status coef_extent(const iwf_plan* p, const void* coef, double threshold, int* need,
+                       cudaStream_t s) {
+  if (!p || !coef || !need) return fail(IWF_ERR_ARG, "iwf_coef_extent: NULL argument");
+  if (!(threshold >= 0.0) || !std::isfinite(threshold))
+    return fail(IWF_ERR_ARG, "iwf_coef_extent: threshold must be finite and >= 0");
+  if (reinterpret_cast<uintptr_t>(coef) & 15)
+    return fail(IWF_ERR_ARG, "iwf_coef_extent: coefficients must be 16-byte aligned");
+  DeviceGuard guard(p->device);
+  int* d_need = nullptr;
+  IWF_CUDA(cudaMalloc((void**)&d_need, IWF_MAX_N * sizeof(int)));
+  iwf_status st = IWF_OK;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((p->g.N + 255) / 256, 8 * 152));
+  if (cudaMemsetAsync(d_need, 0, IWF_MAX_N * sizeof(int), s) != cudaSuccess) st = fail(IWF_ERR_CUDA, "iwf_coef_extent");
+  if (st == IWF_OK) {
+    coef_extent_kernel<<<blocks, 256, 0, s>>>(p->g, reinterpret_cast<const double2*>(coef),
+                                              threshold * threshold, d_need);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) st = fail(IWF_ERR_CUDA, "iwf_coef_extent launch");
+  }
+  if (st == IWF_OK &&
+      (cudaMemcpyAsync(need, d_need, p->g.n * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    st = fail(IWF_ERR_CUDA, "iwf_coef_extent readback");
+  cudaFree(d_need);
+  return st;
 }
 
 }  // namespace iwf
