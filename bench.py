@@ -295,17 +295,22 @@ def cpu_baselines(pb, sweep_budget_s: float = 10.0):
 
 
 SOLVE_RUNS = [("iwfpm_f64", "iwfpm", "f64"), ("iwfpm_mixed", "iwfpm", "c64"),
-              ("pm_f64", "pm", "f64")]
+              ("pm_f64", "pm", "f64"), ("iwfpm_f64_df_dfts", "iwfpm", "f64/df"),
+              ("iwfpm_mixed_df_dfts", "iwfpm", "c64/df")]
 
 
 def time_solves(iwf, torch, local, nev=16, block=24, eps=EPS, maxit=600, runs=None):
     """Time to nev eigenpairs at residual 1e-10 on the 32^4 grid: IWFPM (FP64, then the
-    complex64-then-FP64 mixed mode) and PM on the box [-16,16)^4 (same DOF), FP64."""
+    complex64-then-FP64 mixed mode) and PM on the box [-16,16)^4 (same DOF), FP64; and the
+    two IWFPM modes with double-float DFTs in their complex-double applies ("/df")."""
     out = {"nev": nev, "block": block, "tol": 1e-10, "eps": eps}
     for key, method, prec in (runs or SOLVE_RUNS):
+        prec, _, arith = prec.partition("/")
         pb = W.config_moire(eps=eps, method=method)
         plan = iwf.Plan(pb.P, pb.K, pb.L, method=method, device=local)
         plan.set_potential(pb.modes, pb.coef)
+        if arith:
+            plan.set_arith(arith)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -694,6 +699,36 @@ def run_ours(args):
                         "note": "whole three-pass apply: the block is read and written once per "
                                 "pass and psi is read again by pass C"}}
 
+    # the same FP64 apply with double-float DFTs (IWF_ARITH_DF, pencil path): storage, the
+    # potential and the kinetic term stay FP64, the DFTs run on the FP32 pipes
+    df_apply = None
+    if tune["f64"]["path"] == "pencil":
+        plan.set_arith("df")
+        yd = torch.empty_like(x)
+        for _ in range(3):
+            plan.apply(x, yd)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nrep):
+            plan.apply(x, yd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_df = e0.elapsed_time(e1) / nrep
+        d_ms, d_n = np.zeros(3), np.zeros(3)
+        for _ in range(3):
+            ms3, n3 = plan.apply_profile(x, yd)
+            d_ms += ms3
+            d_n += n3
+        plan.apply(x, yd)
+        plan.set_arith("f64")
+        plan.apply(x, y)
+        diff = float(((yd - y).abs().max() / y.abs().max()).item())
+        df_apply = {"value": pts / (ms_df * 1e-3), "unit": UNIT, "ms_per_step": ms_df,
+                    "speedup_vs_fp64_dfts": ms / ms_df, "max_rel_diff_vs_fp64_dfts": diff,
+                    "pass_ms_per_apply": (d_ms / 3).round(4).tolist(),
+                    "arith": "double-float DFTs (about 48 significant bits) on the FP32 pipes; "
+                             "FP64 storage, potential tables and kinetic term"}
+
     # ablation: the same operator by direct convolution with the potential's 8 folded modes
     # (iwf_apply_stencil), both precisions, against HBM (one read, one write per point)
     stencil = {}
@@ -861,7 +896,8 @@ def run_ours(args):
                    "parallelism": f"replicas{ws}", "schedule": tune,
                    "l2": "inputs 268 MB > 129 MB L2; no flush needed"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "c64_apply": c64, "stencil_ablation": stencil, "long_axis": long_axis,
+        "clocks": clk, "c64_apply": c64, "f64_apply_df_dfts": df_apply,
+        "stencil_ablation": stencil, "long_axis": long_axis,
         "evaluate": evaluate,
         "solve": solve,
         "sweep": sweep,

@@ -461,6 +461,23 @@ iwf_status iwf_plan_set_schedule(iwf_plan* plan, int precision, int threads, int
  * returns IWF_ERR_UNSUPPORTED and leaves the plan unchanged. */
 iwf_status iwf_plan_set_path(iwf_plan* plan, int precision, int path);
 
+/*
+ * Arithmetic of the DFTs of an FP64 (complex double) apply on the pencil path:
+ *   IWF_ARITH_F64  FP64 (the default);
+ *   IWF_ARITH_DF   double-float on the FP32 pipes: each value h + l of two floats (about
+ *                  48 significant bits), split from and joined back to FP64 in integer
+ *                  arithmetic at the pass boundaries. Storage, the potential tables and the
+ *                  kinetic term Lambda psi stay FP64; the DFTs' errors grow from about 2^-53
+ *                  to about 2^-45 of the vector's norm. On this GPU FP64 issues at 1/64 of
+ *                  the FP32 rate, which bounds the FP64 passes.
+ * Applies to iwf_apply, iwf_apply_host, iwf_apply_noalloc and the eigensolvers' complex-
+ * double phase on this plan. IWF_ARITH_DF on a geometry without the pencil path, or with
+ * the path set to IWF_PATH_TILED, returns IWF_ERR_UNSUPPORTED (the tiled kernels compute in
+ * FP64). Library extension: the paper's FFTs are FP64 (MATLAB).
+ */
+enum { IWF_ARITH_F64 = 0, IWF_ARITH_DF = 1 };
+iwf_status iwf_plan_set_arith(iwf_plan* plan, int arith);
+
 /* The schedule iwf_apply will use: sched[4] = {threads, tile_kb, chunk_mb, path}, path
  * being IWF_PATH_TILED or IWF_PATH_PENCIL (IWF_PATH_AUTO resolved for this geometry). */
 iwf_status iwf_plan_get_schedule(const iwf_plan* plan, int precision, int* sched);

@@ -283,6 +283,11 @@ class Plan:
         return {"threads": out[0], "tile_kb": out[1], "chunk_mb": out[2],
                 "path": names[out[3]]}
 
+    def set_arith(self, arith):
+        """iwf_plan_set_arith: "f64" or "df" (double-float DFTs of FP64 applies, pencil path)."""
+        code = {"f64": 0, "df": 1}[arith]
+        self._c.check(self._c.iwf_plan_set_arith(self.handle, code), "iwf_plan_set_arith")
+
     def coef_extent(self, coef, threshold, stream=None):
         """iwf_coef_extent: per axis, the smallest half-width (K'_j, then L'_j) of a window
         with this plan's centring that holds every coefficient with |c_k| >= threshold

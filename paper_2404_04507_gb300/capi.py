@@ -59,6 +59,7 @@ _PROTOS = {
                              C.POINTER(_i), C.POINTER(iwf_plan_opts)]),
     "iwf_plan_destroy": (None, [_vp]),
     "iwf_coef_extent": (_i, [_vp, _vp, C.c_double, C.POINTER(C.c_int), _vp]),
+    "iwf_plan_set_arith": (_i, [_vp, _i]),
     "iwf_plan_trim": (None, [_vp]),
     "iwf_plan_size": (_i, [_vp, C.POINTER(_ll)]),
     "iwf_plan_lens": (_i, [_vp, C.POINTER(_i)]),

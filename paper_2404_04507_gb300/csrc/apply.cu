@@ -455,6 +455,27 @@ __global__ void __launch_bounds__(kLongThreads, 1) pass_long_kernel(PassArgs a) 
 // Bank conflicts: a warp-wide access of 8-byte (16-byte) elements is served in wavefronts of
 // G = 16 (8) lanes; the swizzles make the G element indices of every wavefront distinct
 // modulo G, both when a pencil is written and when the transposed pencil is read.
+// Compute type of the pencil DFTs: the storage type itself, or the double-float dfl for
+// FP64 storage (IWF_ARITH_DF: the FP32 pipes instead of the FP64 one). A shared-memory
+// complex element is 16 bytes in both FP64 forms, so the layouts and swizzles are shared.
+template <typename U> struct SmemCplx;
+template <> struct SmemCplx<double> { using type = double2; };
+template <> struct SmemCplx<float> { using type = float2; };
+template <> struct SmemCplx<dfl> { using type = float4; };
+__device__ __forceinline__ double2 mkc(double r, double i) { return make_double2(r, i); }
+__device__ __forceinline__ float2 mkc(float r, float i) { return make_float2(r, i); }
+__device__ __forceinline__ float4 mkc(dfl r, dfl i) { return make_float4(r.h, r.l, i.h, i.l); }
+__device__ __forceinline__ void unc(double2 v, double& r, double& i) { r = v.x; i = v.y; }
+__device__ __forceinline__ void unc(float2 v, float& r, float& i) { r = v.x; i = v.y; }
+__device__ __forceinline__ void unc(float4 v, dfl& r, dfl& i) { r = dfl(v.x, v.y); i = dfl(v.z, v.w); }
+// storage value -> compute value, and back
+__device__ __forceinline__ void ld_u(double x, double& u) { u = x; }
+__device__ __forceinline__ void ld_u(float x, float& u) { u = x; }
+__device__ __forceinline__ void ld_u(double x, dfl& u) { u = to_dfl(x); }
+__device__ __forceinline__ double st_t(double u) { return u; }
+__device__ __forceinline__ float st_t(float u) { return u; }
+__device__ __forceinline__ double st_t(dfl u) { return from_dfl(u); }
+
 struct PencilArgs {
   const void* in;
   void* out;
@@ -483,9 +504,11 @@ __device__ __forceinline__ int roll_of(int lo, int len) {
 // Pass A (KIND 0) and pass C (KIND 2) over whole slices. A warp owns 32 / L slices; lane
 // (s, p) of it loads grid column p of slice s along axis 0, so each load instruction reads
 // whole 32-element rows of the slice (a permutation of them, because of the roll).
-template <typename T, int L, int KIND>
+template <typename T, int L, int KIND, typename U = T>
 __global__ void __launch_bounds__(256) pencil_ac_kernel(PencilArgs a) {
   using V2 = typename Vec2<T>::type;
+  using SC = typename SmemCplx<U>::type;
+  static_assert(sizeof(SC) == sizeof(V2), "shared-memory element size");
   constexpr int SPW = 32 / L, LL = L * L;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -495,11 +518,11 @@ __global__ void __launch_bounds__(256) pencil_ac_kernel(PencilArgs a) {
   if (pencil_skip(a, vec)) return;
   if (((long long)blockIdx.x * (blockDim.x >> 5) + warp) * SPW >= a.MII) return;  // whole warp idle
   const bool valid = o < a.MII;
-  V2* S = reinterpret_cast<V2*>(smem_raw) + (size_t)threadIdx.x / L * LL;  // this slice's buffer
+  SC* S = reinterpret_cast<SC*>(smem_raw) + (size_t)threadIdx.x / L * LL;  // this slice's buffer
   int off0 = 0, off1 = 0;
   if (valid) { off0 = roll_of(a.lo[2 * o], L); off1 = roll_of(a.lo[2 * o + 1], L); }
   const size_t sbase = (size_t)vec * a.ld + (size_t)o * LL;
-  T xr[L], xi[L];
+  U xr[L], xi[L];
   if (KIND == 0) {
     // window order -> grid: grid (i, p) sits at window ((i + off0) mod L, (p + off1) mod L)
     const V2* in = reinterpret_cast<const V2*>(a.in) + sbase;
@@ -508,19 +531,19 @@ __global__ void __launch_bounds__(256) pencil_ac_kernel(PencilArgs a) {
     for (int i = 0; i < L; ++i) {
       V2 v{};
       if (valid) v = in[((i + off0) & (L - 1)) * L + col];
-      xr[i] = v.x; xi[i] = v.y;
+      ld_u(v.x, xr[i]); ld_u(v.y, xi[i]);
     }
-    Dft<L, +1, T>::run(xr, xi);                         // along axis 0: lane p has column p
+    Dft<L, +1, U>::run(xr, xi);                         // along axis 0: lane p has column p
 #pragma unroll
-    for (int i = 0; i < L; ++i) { V2 v; v.x = xr[i]; v.y = xi[i]; S[i * L + (p ^ i)] = v; }
+    for (int i = 0; i < L; ++i) S[i * L + (p ^ i)] = mkc(xr[i], xi[i]);
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < L; ++j) { const V2 v = S[p * L + (j ^ p)]; xr[j] = v.x; xi[j] = v.y; }
-    Dft<L, +1, T>::run(xr, xi);                         // along axis 1: lane p has row l0 = p
+    for (int j = 0; j < L; ++j) unc(S[p * L + (j ^ p)], xr[j], xi[j]);
+    Dft<L, +1, U>::run(xr, xi);                         // along axis 1: lane p has row l0 = p
     if (valid) {
       V2* out = reinterpret_cast<V2*>(a.out) + sbase;
 #pragma unroll
-      for (int j = 0; j < L; ++j) { V2 v; v.x = xr[j]; v.y = xi[j]; out[j * L + p] = v; }
+      for (int j = 0; j < L; ++j) { V2 v; v.x = st_t(xr[j]); v.y = st_t(xi[j]); out[j * L + p] = v; }
     }
   } else {
     const V2* in = reinterpret_cast<const V2*>(a.in) + sbase;
@@ -528,15 +551,15 @@ __global__ void __launch_bounds__(256) pencil_ac_kernel(PencilArgs a) {
     for (int j = 0; j < L; ++j) {
       V2 v{};
       if (valid) v = in[j * L + p];
-      xr[j] = v.x; xi[j] = v.y;
+      ld_u(v.x, xr[j]); ld_u(v.y, xi[j]);
     }
-    Dft<L, -1, T>::run(xr, xi);                         // along axis 1 for row l0 = p
+    Dft<L, -1, U>::run(xr, xi);                         // along axis 1 for row l0 = p
 #pragma unroll
-    for (int j = 0; j < L; ++j) { V2 v; v.x = xr[j]; v.y = xi[j]; S[p * L + (j ^ p)] = v; }
+    for (int j = 0; j < L; ++j) S[p * L + (j ^ p)] = mkc(xr[j], xi[j]);
     __syncwarp();
 #pragma unroll
-    for (int i = 0; i < L; ++i) { const V2 v = S[i * L + (p ^ i)]; xr[i] = v.x; xi[i] = v.y; }
-    Dft<L, -1, T>::run(xr, xi);                         // along axis 0 for column p
+    for (int i = 0; i < L; ++i) unc(S[i * L + (p ^ i)], xr[i], xi[i]);
+    Dft<L, -1, U>::run(xr, xi);                         // along axis 0 for column p
     if (valid) {
       // grid -> window order, + Lambda psi at the same window positions. psi and H psi never
       // overlap (checked on the host), so the loads of a batch are all issued before its
@@ -559,7 +582,7 @@ __global__ void __launch_bounds__(256) pencil_ac_kernel(PencilArgs a) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           const int w = ((i0 + u + off0) & (L - 1)) * L + col;
-          V2 r; r.x = xr[i0 + u] + l[u] * q[u].x; r.y = xi[i0 + u] + l[u] * q[u].y;
+          V2 r; r.x = st_t(xr[i0 + u]) + l[u] * q[u].x; r.y = st_t(xi[i0 + u]) + l[u] * q[u].y;
           out[w] = r;
         }
       }
@@ -773,15 +796,17 @@ __device__ __forceinline__ int pencil_sw(int a, int c, int k) {
 // Pass B (in place) on a tile of C consecutive slice positions x all LII^2 k_II points.
 // Thread (a, c) first holds the pencil along k_II axis 0 at axis-1 window coordinate a; after
 // the transpose, thread (k, c) holds the pencil along k_II axis 1 at axis-0 grid index k.
-template <typename T, int L, int C>
+template <typename T, int L, int C, typename U = T>
 __global__ void __launch_bounds__(C * L) pencil_b_kernel(PencilArgs a) {
   using V2 = typename Vec2<T>::type;
+  using SC = typename SmemCplx<U>::type;
+  static_assert(sizeof(SC) == sizeof(V2) && sizeof(U) == sizeof(T), "shared-memory sizes");
   constexpr int LL = L * L, H = L / 2, G = wave_lanes<T>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  V2* S = reinterpret_cast<V2*>(smem_raw);
-  T* vI = reinterpret_cast<T*>(S + C * LL);   // C slice positions
-  T* v0 = vI + C;                             // k_II axis 0 table (L)
-  T* v1 = v0 + L;                             // k_II axis 1 table (L)
+  SC* S = reinterpret_cast<SC*>(smem_raw);
+  U* vI = reinterpret_cast<U*>(S + C * LL);   // C slice positions
+  U* v0 = vI + C;                             // k_II axis 0 table (L)
+  U* v1 = v0 + L;                             // k_II axis 1 table (L)
   const int c = threadIdx.x % C, ta = threadIdx.x / C;
   const long long c0 = (long long)blockIdx.x * C;
   const int vec = blockIdx.y;
@@ -792,14 +817,14 @@ __global__ void __launch_bounds__(C * L) pencil_b_kernel(PencilArgs a) {
     const long long tb = (long long)prob * a.pot.tab_stride;
     if (threadIdx.x < C) {
       const int pos = (int)(c0 + threadIdx.x);      // slice layout: pos = l1 * LI + l0
-      vI[threadIdx.x] = pot_const<T>(a.pot) + pot_tab<T>(a.pot, tb + a.pot.tab_off[0] + pos % LI) +
-                        pot_tab<T>(a.pot, tb + a.pot.tab_off[1] + pos / LI);
+      ld_u(pot_const<T>(a.pot) + pot_tab<T>(a.pot, tb + a.pot.tab_off[0] + pos % LI) +
+               pot_tab<T>(a.pot, tb + a.pot.tab_off[1] + pos / LI), vI[threadIdx.x]);
     } else if (threadIdx.x < C + L) {
       const int l = threadIdx.x - C;
-      v0[l] = pot_tab<T>(a.pot, tb + a.pot.tab_off[2] + l);
+      ld_u(pot_tab<T>(a.pot, tb + a.pot.tab_off[2] + l), v0[l]);
     } else if (threadIdx.x < C + 2 * L) {
       const int l = threadIdx.x - C - L;
-      v1[l] = pot_tab<T>(a.pot, tb + a.pot.tab_off[3] + l);
+      ld_u(pot_tab<T>(a.pot, tb + a.pot.tab_off[3] + l), v1[l]);
     }
   }
   // in place (a.in == a.out): every load of the tile precedes the first barrier, every store
@@ -812,63 +837,60 @@ __global__ void __launch_bounds__(C * L) pencil_b_kernel(PencilArgs a) {
   // recomputes the 32 indices instead of keeping them live across the DFTs.
   constexpr int M = (C >= G) ? 0 : G / C - 1;     // bits of k that enter f
   int t0 = c * LL + pencil_sw<C, G>(ta, c, 0);     // (i, ta): (t0 ^ (i & M)) + i * L
-  T xr[L], xi[L];
+  U xr[L], xi[L];
   // grid index i along k_II axis 0 sits at window row (i + L/2) mod L (roll by L_j)
 #pragma unroll
   for (int i = 0; i < L; ++i) {
     const V2 v = col[((i + H) & (L - 1)) * rstride];
-    xr[i] = v.x; xi[i] = v.y;
+    ld_u(v.x, xr[i]); ld_u(v.y, xi[i]);
   }
-  Dft<L, +1, T>::run(xr, xi);
+  Dft<L, +1, U>::run(xr, xi);
 #pragma unroll
   for (int i = 0; i < L; ++i) {
-    V2 v; v.x = xr[i]; v.y = xi[i];
-    S[(t0 ^ (i & M)) + i * L] = v;
+    S[(t0 ^ (i & M)) + i * L] = mkc(xr[i], xi[i]);
   }
   __syncthreads();
   const int k = ta;
   int r1 = (c * LL + k * L) | pencil_sw<C, G>(0, c, k);   // (k, a): r1 ^ a
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const V2 v = S[r1 ^ ((j + H) & (L - 1))];
-    xr[j] = v.x; xi[j] = v.y;
+    unc(S[r1 ^ ((j + H) & (L - 1))], xr[j], xi[j]);
   }
-  Dft<L, +1, T>::run(xr, xi);
+  Dft<L, +1, U>::run(xr, xi);
   // x V(y_l) / N at l_II = (k, j) and the tile column's k_I grid point
   if (a.pot.kind == 1) {
-    const T base = vI[c] + v0[k];
+    const U base = vI[c] + v0[k];
 #pragma unroll
-    for (int j = 0; j < L; ++j) { const T v = base + v1[j]; xr[j] *= v; xi[j] *= v; }
+    for (int j = 0; j < L; ++j) { const U v = base + v1[j]; xr[j] = xr[j] * v; xi[j] = xi[j] * v; }
   } else {
     const int pos = (int)(c0 + c);
     const long long lI = (long long)(pos % LI) * LI + pos / LI;   // natural k_I order
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-      const T v = pot_grid<T>(a.pot, (long long)(k * L + j) * a.MI + lI);
-      xr[j] *= v; xi[j] *= v;
+      U v;
+      ld_u(pot_grid<T>(a.pot, (long long)(k * L + j) * a.MI + lI), v);
+      xr[j] = xr[j] * v; xi[j] = xi[j] * v;
     }
   }
-  Dft<L, -1, T>::run(xr, xi);
+  Dft<L, -1, U>::run(xr, xi);
   asm volatile("" : "+r"(r1));
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    V2 v; v.x = xr[j]; v.y = xi[j];
-    S[r1 ^ ((j + H) & (L - 1))] = v;
+    S[r1 ^ ((j + H) & (L - 1))] = mkc(xr[j], xi[j]);
   }
   __syncthreads();
   asm volatile("" : "+r"(t0));
 #pragma unroll
   for (int i = 0; i < L; ++i) {
-    const V2 v = S[(t0 ^ (i & M)) + i * L];
-    xr[i] = v.x; xi[i] = v.y;
+    unc(S[(t0 ^ (i & M)) + i * L], xr[i], xi[i]);
   }
-  Dft<L, -1, T>::run(xr, xi);
+  Dft<L, -1, U>::run(xr, xi);
   // make the tile pointer opaque so that the load addresses are recomputed here instead of
   // being kept live across the DFTs
   asm volatile("" : "+l"(col));
 #pragma unroll
   for (int i = 0; i < L; ++i) {
-    V2 v; v.x = xr[i]; v.y = xi[i];
+    V2 v; v.x = st_t(xr[i]); v.y = st_t(xi[i]);
     col[((i + H) & (L - 1)) * rstride] = v;
   }
 }
@@ -884,6 +906,7 @@ iwf_status init_twiddles(int device) {
   if (device >= 0 && device < 64 && g_tw_ready[device]) return IWF_OK;
   std::vector<double2> h64(kTwTotal);
   std::vector<float2> h32(kTwTotal);
+  std::vector<float4> hdf(kTwTotal);
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int len = 1; len <= IWF_MAX_LEN; ++len) {
     for (int j = 0; j < len; ++j) {
@@ -895,10 +918,14 @@ iwf_status init_twiddles(int device) {
       else { const long double t = two_pi * j / len; c = cosl(t); s = sinl(t); }
       h64[tw_off(len) + j] = make_double2((double)c, (double)s);
       h32[tw_off(len) + j] = make_float2((float)c, (float)s);
+      const float ch = (float)c, sh = (float)s;
+      hdf[tw_off(len) + j] = make_float4(ch, (float)(c - (long double)ch), sh,
+                                         (float)(s - (long double)sh));
     }
   }
   IWF_CUDA(cudaMemcpyToSymbol(c_tw64, h64.data(), sizeof(double2) * kTwTotal));
   IWF_CUDA(cudaMemcpyToSymbol(c_tw32, h32.data(), sizeof(float2) * kTwTotal));
+  IWF_CUDA(cudaMemcpyToSymbol(c_twdf, hdf.data(), sizeof(float4) * kTwTotal));
   if (device >= 0 && device < 64) g_tw_ready[device] = true;
   return IWF_OK;
 }
@@ -1063,7 +1090,7 @@ iwf_status persistent_ctas(K* kernel, int threads, size_t smem, OccCache* cache,
 // units).
 template <typename T, int KIND> constexpr bool use_pipe() { return sizeof(T) == 4 && KIND == 2; }
 
-template <typename T, int L, int KIND>
+template <typename T, int L, int KIND, typename U = T>
 iwf_status launch_pencil_direct(const PencilArgs& a, int nvec, cudaStream_t stream,
                                 PassTimer* timer) {
   using V2 = typename Vec2<T>::type;
@@ -1071,10 +1098,10 @@ iwf_status launch_pencil_direct(const PencilArgs& a, int nvec, cudaStream_t stre
   constexpr int per_cta = threads / 32 * (32 / L);          // slices per CTA
   const size_t smem = (size_t)threads * L * sizeof(V2);
   static size_t allowed[64] = {};
-  IWF_TRY(allow_smem(pencil_ac_kernel<T, L, KIND>, smem, allowed));
+  IWF_TRY(allow_smem(pencil_ac_kernel<T, L, KIND, U>, smem, allowed));
   dim3 grid((unsigned)((a.MII + per_cta - 1) / per_cta), (unsigned)nvec);
   if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
-  pencil_ac_kernel<T, L, KIND><<<grid, threads, smem, stream>>>(a);
+  pencil_ac_kernel<T, L, KIND, U><<<grid, threads, smem, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return timer ? stop_timer(timer, KIND, stream) : IWF_OK;
@@ -1102,42 +1129,42 @@ iwf_status launch_pencil_c_pipe(const PencilArgs& a, int nvec, int* err, cudaStr
   return timer ? stop_timer(timer, 2, stream) : IWF_OK;
 }
 
-template <typename T, int L, int KIND>
+template <typename T, int L, int KIND, typename U = T>
 iwf_status launch_pencil_ac(const PencilArgs& a, int nvec, int* err, cudaStream_t stream,
                             PassTimer* timer) {
   if constexpr (use_pipe<T, KIND>()) return launch_pencil_c_pipe<T, L>(a, nvec, err, stream, timer);
-  else return launch_pencil_direct<T, L, KIND>(a, nvec, stream, timer);
+  else return launch_pencil_direct<T, L, KIND, U>(a, nvec, stream, timer);
 }
 
-template <typename T, int L>
+template <typename T, int L, typename U = T>
 iwf_status launch_pencil_b(const PencilArgs& a, int nvec, cudaStream_t stream, PassTimer* timer) {
   using V2 = typename Vec2<T>::type;
   constexpr int C = pencil_threads<T>() / L;
   const size_t smem = (size_t)C * L * L * sizeof(V2) + (size_t)(C + 2 * L) * sizeof(T);
   static size_t allowed[64] = {};
-  IWF_TRY(allow_smem(pencil_b_kernel<T, L, C>, smem, allowed));
+  IWF_TRY(allow_smem(pencil_b_kernel<T, L, C, U>, smem, allowed));
   if (a.MI % C) return fail(IWF_ERR_UNSUPPORTED, "pencil pass B: slice not a multiple of the tile");
   dim3 grid((unsigned)(a.MI / C), (unsigned)nvec);
   if (timer) IWF_CUDA(cudaEventRecord(timer->ev[0], stream));
-  pencil_b_kernel<T, L, C><<<grid, C * L, smem, stream>>>(a);
+  pencil_b_kernel<T, L, C, U><<<grid, C * L, smem, stream>>>(a);
   IWF_CUDA(cudaGetLastError());
   count_launch();
   return timer ? stop_timer(timer, 1, stream) : IWF_OK;
 }
 
-// One chunk of vectors through the three pencil passes.
-template <typename T>
+// One chunk of vectors through the three pencil passes (DFTs in the compute type U).
+template <typename T, typename U = T>
 iwf_status pencil_chunk(PencilArgs a, int LI, int LII, const void* in, void* wk, void* out,
                         const void* lam, int nv, int* err, cudaStream_t stream, PassTimer* timer) {
   a.in = in; a.out = wk;
-  IWF_TRY(LI == 16 ? (launch_pencil_ac<T, 16, 0>(a, nv, err, stream, timer))
-                   : (launch_pencil_ac<T, 32, 0>(a, nv, err, stream, timer)));
+  IWF_TRY(LI == 16 ? (launch_pencil_ac<T, 16, 0, U>(a, nv, err, stream, timer))
+                   : (launch_pencil_ac<T, 32, 0, U>(a, nv, err, stream, timer)));
   a.in = wk; a.out = wk;
-  IWF_TRY(LII == 16 ? (launch_pencil_b<T, 16>(a, nv, stream, timer))
-                    : (launch_pencil_b<T, 32>(a, nv, stream, timer)));
+  IWF_TRY(LII == 16 ? (launch_pencil_b<T, 16, U>(a, nv, stream, timer))
+                    : (launch_pencil_b<T, 32, U>(a, nv, stream, timer)));
   a.in = wk; a.out = out; a.psi = in; a.lam = lam;
-  return LI == 16 ? launch_pencil_ac<T, 16, 2>(a, nv, err, stream, timer)
-                  : launch_pencil_ac<T, 32, 2>(a, nv, err, stream, timer);
+  return LI == 16 ? launch_pencil_ac<T, 16, 2, U>(a, nv, err, stream, timer)
+                  : launch_pencil_ac<T, 32, 2, U>(a, nv, err, stream, timer);
 }
 
 template <typename T>
@@ -1244,9 +1271,17 @@ iwf_status apply_typed(iwf_plan* p, const void* psi, void* hpsi, int nvec, cudaS
     for (int v0 = 0; v0 < nvec; v0 += chunk) {
       const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
       pa.vec_base = v0;
-      IWF_TRY(pencil_chunk<T>(pa, LI, LII, reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N,
-                              work, reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N, Cp.lam, nv,
-                              p->d_apply_err, stream, timer));
+      const void* cin = reinterpret_cast<const V2*>(psi) + (size_t)v0 * g.N;
+      void* cout = reinterpret_cast<V2*>(hpsi) + (size_t)v0 * g.N;
+      if constexpr (sizeof(T) == 8) {
+        if (p->fft_arith == IWF_ARITH_DF) {
+          IWF_TRY((pencil_chunk<T, dfl>(pa, LI, LII, cin, work, cout, Cp.lam, nv, p->d_apply_err,
+                                        stream, timer)));
+          continue;
+        }
+      }
+      IWF_TRY(pencil_chunk<T>(pa, LI, LII, cin, work, cout, Cp.lam, nv, p->d_apply_err, stream,
+                              timer));
     }
     return IWF_OK;
   }
@@ -1353,7 +1388,9 @@ iwf_status autotune_impl(iwf_plan* p, int precision, int nvec, double* best_ms, 
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms / 3 < best_t) { best_t = ms / 3; bt = th; bk = tk; bc = ch; bp = path; }
   };
-  if (saved_path != IWF_PATH_PENCIL)
+  // double-float DFTs exist on the pencil path only: no tiled candidates then
+  const bool df_only = precision == IWF_PREC_F64 && p->fft_arith == IWF_ARITH_DF;
+  if (saved_path != IWF_PATH_PENCIL && !df_only)
     for (int th : threads)
       for (int tk : tiles)
         for (int ch : chunks) trial(IWF_PATH_TILED, th, tk, ch);
@@ -1428,7 +1465,22 @@ iwf_status set_path_impl(iwf_plan* p, int precision, int path) {
     return fail(IWF_ERR_UNSUPPORTED,
                 "iwf_plan_set_path: the pencil path needs n = 4, d = 2 and two equal axis "
                 "lengths per group, each 16 or 32");
+  if (path == IWF_PATH_TILED && precision == IWF_PREC_F64 && p->fft_arith == IWF_ARITH_DF)
+    return fail(IWF_ERR_UNSUPPORTED,
+                "iwf_plan_set_path: double-float DFTs are set on this plan and need the pencil path");
   p->path[precision == IWF_PREC_F64 ? 0 : 1] = path;
+  return IWF_OK;
+}
+
+iwf_status set_arith_impl(iwf_plan* p, int arith) {
+  if (arith != IWF_ARITH_F64 && arith != IWF_ARITH_DF)
+    return fail(IWF_ERR_ARG, "iwf_plan_set_arith: unknown arithmetic");
+  int LI = 0, LII = 0;
+  if (arith == IWF_ARITH_DF && (!pencil_geometry(p->g, &LI, &LII) || p->path[0] == IWF_PATH_TILED))
+    return fail(IWF_ERR_UNSUPPORTED,
+                "iwf_plan_set_arith: double-float DFTs need the pencil path (n = 4, d = 2, two "
+                "equal axis lengths per group, each 16 or 32)");
+  p->fft_arith = arith;
   return IWF_OK;
 }
 

@@ -338,6 +338,12 @@ iwf_status iwf_plan_set_path(iwf_plan* p, int precision, int path) {
   return set_path_impl(p, precision, path);
 }
 
+iwf_status iwf_plan_set_arith(iwf_plan* p, int arith) {
+  clear_error();
+  if (!p) return fail(IWF_ERR_ARG, "iwf_plan_set_arith: NULL plan");
+  return set_arith_impl(p, arith);
+}
+
 iwf_status iwf_plan_get_schedule(const iwf_plan* p, int precision, int* sched) {
   clear_error();
   if (!p) return fail(IWF_ERR_ARG, "iwf_plan_get_schedule: NULL plan");

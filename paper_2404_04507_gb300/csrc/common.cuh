@@ -174,6 +174,8 @@ struct iwf_plan {
   // apply kernels per precision: IWF_PATH_AUTO (pencil path where the geometry allows it),
   // IWF_PATH_TILED or IWF_PATH_PENCIL
   int path[2] = {IWF_PATH_AUTO, IWF_PATH_AUTO};
+  // DFT arithmetic of FP64 applies on the pencil path (IWF_ARITH_F64 or IWF_ARITH_DF)
+  int fft_arith = IWF_ARITH_F64;
   // eigensolver workspace of iwf_eigensolve / iwf_batch_eigensolve, kept between solves: the
   // buffers in the order a solve requests them, each reused while large enough
   struct SolveBuf { void* ptr; size_t bytes; };
@@ -224,6 +226,7 @@ iwf_status set_path_impl(iwf_plan* p, int precision, int path);
 // a pipelined apply kernel gave up waiting for one of its copies.
 iwf_status check_apply_error(iwf_plan* p, cudaStream_t stream);
 iwf_status get_schedule_impl(const iwf_plan* p, int precision, int* sched);
+iwf_status set_arith_impl(iwf_plan* p, int arith);
 void count_launch();
 long long launch_count();
 iwf_status build_window_tables(iwf_plan* p);          // lo table, Lambda; sets d_err on ties

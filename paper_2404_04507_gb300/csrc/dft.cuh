@@ -18,9 +18,11 @@ namespace iwf {
 
 constexpr int kTwTotal = IWF_MAX_LEN * (IWF_MAX_LEN + 1) / 2;  // sum of len over 1..32
 
-// entry (len, j) at len*(len-1)/2 + j holds (cos 2 pi j/len, sin 2 pi j/len)
+// entry (len, j) at len*(len-1)/2 + j holds (cos 2 pi j/len, sin 2 pi j/len); the
+// double-float table holds (cos.h, cos.l, sin.h, sin.l)
 static __constant__ double2 c_tw64[kTwTotal];
 static __constant__ float2 c_tw32[kTwTotal];
+static __constant__ float4 c_twdf[kTwTotal];
 
 __host__ __device__ constexpr int tw_off(int len) { return len * (len - 1) / 2; }
 
@@ -39,12 +41,109 @@ __host__ __device__ constexpr int radix_of(int n) {
          : n;
 }
 
+// Double-float scalar for the DFTs of an FP64-storage apply run on the FP32 pipes: the value
+// h + l with |l| <= ulp(h) / 2, about 48 significant bits. Addition keeps the rounding error
+// of the high parts by Knuth's TwoSum and adds the low parts to it (no cancellation-proof
+// renormalisation: the error stays below about 2^-45 of |a| + |b|, the norm-wise bound an FFT
+// needs); multiplication forms the high product exactly with fma (Dekker/Kahan).
+struct dfl {
+  float h, l;
+  dfl() = default;
+  __device__ __forceinline__ constexpr dfl(float a, float b) : h(a), l(b) {}
+  __device__ __forceinline__ explicit constexpr dfl(int z) : h((float)z), l(0.f) {}
+};
+__device__ __forceinline__ dfl dfl_quick(float s, float e) {
+  const float h = s + e;
+  return dfl(h, e - (h - s));
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  return dfl_quick(s, e);
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.h, -a.l); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + dfl(-b.h, -b.l); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return dfl_quick(p, e);
+}
+__device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { a = a + b; return a; }
+
+// FP64 <-> double-float in integer arithmetic (no FP64 instruction: on this GPU those issue
+// at 1/64 of the FP32 rate). to_dfl: h = x rounded to 24 significant bits (ties away from
+// zero), l = the exact remainder rounded to a float; values below 2^-100 in magnitude, and
+// denormals, become 0 (an apply's vectors are normalised; such entries are far below the
+// double-float resolution of any vector that holds them), values above 2^127 saturate.
+__device__ __forceinline__ dfl to_dfl(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  if (e < 1023 - 100) return dfl(0.f, 0.f);
+  const unsigned int sign = hi & 0x80000000u;
+  const int fe = e < 1023 + 127 ? e - 1023 + 127 : 254;
+  // top 23 stored mantissa bits and the 29 below them; round on bit 28
+  const unsigned int m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned int rest = lo & 0x1FFFFFFFu;
+  const unsigned int up = rest >> 28;                     // 1: round the magnitude up
+  const unsigned int hb = sign | ((unsigned int)fe << 23) | m23;
+  const float h = __uint_as_float(hb + up);               // a carry moves into the exponent
+  // remainder x - h = (rest - up 2^29) 2^(e - 1075), |.| <= 2^28 units: exact as an int,
+  // rounded once to a float, scaled by 2^(e - 1075) through its exponent field
+  const int r = (int)rest - (int)(up << 29);
+  if (r == 0) return dfl(h, 0.f);
+  float l = (float)r;                                     // |l| < 2^29: exponent <= 127 + 28
+  const int le = (int)((__float_as_uint(l) >> 23) & 0xFFu) + (e - 1075);
+  l = le > 0 ? __uint_as_float(__float_as_uint(l) + (unsigned int)((e - 1075) << 23)) : 0.f;
+  return dfl(h, sign ? -l : l);
+}
+// h + l rounded to FP64: the float h widened exactly, l added at its place below h's last
+// bit with one 64-bit integer add and a final round on the dropped bits (|l| <= ulp(h) / 2).
+__device__ __forceinline__ double from_dfl(dfl v) {
+  const unsigned int hb = __float_as_uint(v.h);
+  const int fe = (int)((hb >> 23) & 0xFFu);
+  if (fe == 0) return 0.0;                                // h = 0 (or a denormal: below 2^-126)
+  const unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
+  // |h| as a 53-bit significand M (implicit bit included) times 2^(fe - 127 - 52)
+  long long M = (long long)(((hb & 0x7FFFFFu) | 0x800000u)) << 29;
+  const unsigned int lb = __float_as_uint(v.l);
+  const int le = (int)((lb >> 23) & 0xFFu);
+  if (le != 0) {
+    // l = +-ml 2^(le - 127 - 23); in units of 2^(fe - 127 - 52): shift by (le - 23) - (fe - 52)
+    long long ml = (long long)((lb & 0x7FFFFFu) | 0x800000u);
+    const int sh = (le - 23) - (fe - 52);
+    if (sh >= 0) ml <<= sh;
+    else ml = sh > -64 ? ((ml >> (-sh - 1)) + 1) >> 1 : 0;  // round half up on the dropped bits
+    // the sign of l relative to h
+    M += ((lb ^ hb) & 0x80000000u) ? -ml : ml;
+  }
+  // renormalise M (it stays within [2^51, 2^54) since |l| <= ulp(h) / 2)
+  int de = 0;
+  if (M >= (1LL << 53)) { M = (M + 1) >> 1; de = 1; }
+  else if (M < (1LL << 52)) { M <<= 1; de = -1; }
+  const long long e64 = (long long)fe - 127 + 1023 + de;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e64 << 52) |
+                                           ((unsigned long long)M & 0xFFFFFFFFFFFFFull)));
+}
+
 template <typename T> __device__ __forceinline__ T tw_cos(int off);
 template <typename T> __device__ __forceinline__ T tw_sin(int off);
 template <> __device__ __forceinline__ double tw_cos<double>(int off) { return c_tw64[off].x; }
 template <> __device__ __forceinline__ double tw_sin<double>(int off) { return c_tw64[off].y; }
 template <> __device__ __forceinline__ float tw_cos<float>(int off) { return c_tw32[off].x; }
 template <> __device__ __forceinline__ float tw_sin<float>(int off) { return c_tw32[off].y; }
+template <> __device__ __forceinline__ dfl tw_cos<dfl>(int off) {
+  const float4 t = c_twdf[off];
+  return dfl(t.x, t.y);
+}
+template <> __device__ __forceinline__ dfl tw_sin<dfl>(int off) {
+  const float4 t = c_twdf[off];
+  return dfl(t.z, t.w);
+}
 
 template <int S, typename T> __device__ __forceinline__ T sgn(T x) {
   if constexpr (S > 0) return x; else return -x;

@@ -232,6 +232,54 @@ def test_pencil_and_tiled_paths_agree_full_size(iwf, prec):
         assert np.max(np.abs(got_p[:, c] - want)) <= tol * np.max(np.abs(want))
 
 
+# Double-float DFTs of an FP64 apply (IWF_ARITH_DF): storage, potential and kinetic term stay
+# FP64, the DFTs carry about 48 bits; same element-wise tolerance as the FP64 path.
+@pytest.mark.parametrize("name", list(PENCIL))
+def test_double_float_dfts_match_oracle(iwf, name):
+    pb = PENCIL[name]
+    plan = _plan(iwf, pb)
+    plan.set_arith("df")
+    win, Vg = _oracle(pb)
+    X = W.random_block(win.N, 3, seed=22)
+    X[:, 1] *= 10.0 ** np.random.default_rng(4).uniform(-40, 0, size=win.N)   # wide range
+    got = _gpu_apply(plan, X, torch.complex128)
+    want = O.apply_stencil(win, Vg, X)
+    for c in range(3):
+        err = np.max(np.abs(got[:, c] - want[:, c])) / np.max(np.abs(want[:, c]))
+        assert err <= TOL64, (c, err)
+
+
+@pytest.mark.parametrize("eps", [0.5, 5.0])
+def test_double_float_dfts_full_size(iwf, eps):
+    pb = W.config_moire(eps=eps)
+    plan = _plan(iwf, pb)
+    X = W.random_block(plan.N, 16, seed=6)
+    got64 = _gpu_apply(plan, X, torch.complex128)
+    plan.set_arith("df")
+    gotdf = _gpu_apply(plan, X, torch.complex128)
+    assert np.max(np.abs(gotdf - got64)) <= TOL64 * np.max(np.abs(got64))
+    plan.set_arith("f64")
+    assert np.array_equal(_gpu_apply(plan, X[:, :2], torch.complex128), got64[:, :2])
+
+
+def test_double_float_dfts_need_the_pencil_path(iwf):
+    from paper_2404_04507_gb300 import capi
+    plan = _plan(iwf, PROBS["moire_ragged"])
+    with pytest.raises(capi.IwfError) as e:
+        plan.set_arith("df")
+    assert e.value.status == -10
+    plan = _plan(iwf, PENCIL["moire16"])
+    plan.set_arith("df")
+    with pytest.raises(capi.IwfError) as e:
+        plan.set_path("f64", "tiled")
+    assert e.value.status == -10
+    plan.set_arith("f64")
+    plan.set_path("f64", "tiled")
+    with pytest.raises(capi.IwfError) as e:
+        plan.set_arith("df")
+    assert e.value.status == -10
+
+
 def test_path_selection(iwf):
     from paper_2404_04507_gb300 import capi
     plan = _plan(iwf, PROBS["moire_ragged"])

@@ -189,3 +189,19 @@ def test_qse3d_full_size_config3():
     ev, X, res, info = plan.eigensolve(16, block=24, precision="c64", maxit=600, seed=3)
     assert info["converged"] == 1 and np.max(res) <= 1e-10
     assert _close(ev, ref), np.max(np.abs(ev - ref))
+
+
+def test_double_float_dfts_in_the_eigensolver(iwf):
+    # the complex-double phase with double-float DFTs (IWF_ARITH_DF) reaches the same
+    # eigenvalues as with FP64 DFTs, at the same residual
+    pb = W.config_moire(eps=2.0, K=8, L=8)
+    ref = iwf.Plan(pb.P, pb.K, pb.L)
+    ref.set_potential(pb.modes, pb.coef)
+    ev0, _, res0, info0 = ref.eigensolve(8, block=12, tol=1e-10)
+    plan = iwf.Plan(pb.P, pb.K, pb.L)
+    plan.set_potential(pb.modes, pb.coef)
+    plan.set_arith("df")
+    ev1, _, res1, info1 = plan.eigensolve(8, block=12, tol=1e-10)
+    assert info1["converged"] == 1 and np.all(res1 <= 1e-10)
+    assert np.all(np.abs(ev1 - ev0) <= 1e-10 * np.maximum(1.0, np.abs(ev0)))
+
