@@ -419,28 +419,39 @@ def time_batch_sweep(iwf, torch, local, count=256, single_sample=8):
                                               seed=7, raise_noconv=False)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    order = np.argsort(kl, kind="stable")
-    pick = [int(order[int(round(j * (count - 1) / (single_sample - 1)))]) for j in range(single_sample)]
-    t_single = 0.0
-    for i in pick:
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        plans[i].eigensolve(16, block=24, tol=1e-10, precision="c64", seed=7, raise_noconv=False)
-        torch.cuda.synchronize()
-        t_single += time.perf_counter() - t1
+    red = reduce_max if (ws > 1 and reduce_max) else (lambda v: v)
+    t_batch = red(t_batch)
+    not_conv = red(0.0 if info["converged"] else 1.0)
+    max_resid = red(float(np.max(res)))
+    max_iters = int(red(float(np.max(iters))))
+    one = None
+    if ws == 1:
+        order = np.argsort(kl, kind="stable")
+        pick = [int(order[int(round(j * (count - 1) / (single_sample - 1)))])
+                for j in range(single_sample)]
+        t_single = 0.0
+        for i in pick:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            plans[i].eigensolve(16, block=24, tol=1e-10, precision="c64", seed=7,
+                                raise_noconv=False)
+            torch.cuda.synchronize()
+            t_single += time.perf_counter() - t1
+        one = {"problems": single_sample, "seconds": t_single,
+               "solves_per_s": single_sample / t_single,
+               "sample": f"problems {pick} (spread over K = L)"}
     sizes = {int(k): int((2 * k) ** 4) for k in np.unique(kl)}
     for p in plans:
         p.close()
     return {"problems": count, "K=L range": [int(kl.min()), int(kl.max())],
             "dof_range": [int((2 * kl.min()) ** 4), int((2 * kl.max()) ** 4)],
-            "nev": 16, "block": 24, "tol": 1e-10, "precision": "mixed",
+            "nev": 16, "block": 24, "tol": 1e-10, "precision": "mixed", "ranks": ws,
             "batched": {"seconds": t_batch, "solves_per_s": count / t_batch,
-                        "converged": bool(info["converged"]),
-                        "max_resid": float(np.max(res)), "max_iters": int(np.max(iters)),
-                        "call": "iwf_batch_solve (one call, plans grouped by window)"},
-            "one_by_one_sample": {"problems": single_sample, "seconds": t_single,
-                                  "solves_per_s": single_sample / t_single,
-                                  "sample": f"problems {pick} (spread over K = L)"},
+                        "converged": not_conv == 0.0,
+                        "max_resid": max_resid, "max_iters": max_iters,
+                        "call": "iwf_batch_solve (one call per rank, plans grouped by window; "
+                                "problems partitioned by DOF over the ranks)"},
+            "one_by_one_sample": one,
             "windows": {str(k): int(np.sum(kl == k)) for k in sizes}}
 
 
@@ -880,7 +891,8 @@ def run_ours(args):
     config3 = None if (args.no_solve or args.no_config3) else time_config3(iwf, torch, local)
     contractions = None if args.no_solve else time_contractions(iwf, torch, local)
     pm_acc = None if (args.no_solve or args.no_pm_accuracy) else time_pm_equal_accuracy(iwf, torch, local)
-    sweep256 = None if (args.no_solve or args.no_sweep) else time_batch_sweep(iwf, torch, local)
+    sweep256 = None if (args.no_solve or args.no_sweep) else time_batch_sweep(
+        iwf, torch, local, ws=ws, rank=rank, reduce_max=max_over_ranks)
     warm = None if (args.no_solve or args.no_warmstart) else time_warmstart(iwf, torch, local)
 
     if rank != 0:
