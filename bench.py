@@ -400,15 +400,19 @@ def time_config3(iwf, torch, local, maxit=600):
             "per_result_rel_err": [float(v) for v in err]}
 
 
-def time_batch_sweep(iwf, torch, local, count=256, single_sample=8):
+def time_batch_sweep(iwf, torch, local, count=256, single_sample=8, ws=1, rank=0,
+                     reduce_max=None):
     """Config 4 as stated: 256 solves of the moire QSE with eps ~ U[0.1, 10], phases ~
     U[0, 2pi)^4 and cutoff c ~ U[8, 20] -> K = L = floor(0.65 c + 1/2) (seed 4), 16 pairs to
     residual 1e-10, mixed precision, through one iwf_batch_solve call (uneven windows:
-    (2K)^4 from 10^4 to 4.6 x 10^5 points). One-by-one solves are timed on a sample spread
-    over the window sizes."""
+    (2K)^4 from 10^4 to 4.6 x 10^5 points). With several ranks the problems are partitioned
+    by DOF (longest first) and every rank solves its share; the time is the slowest rank's.
+    One-by-one solves are timed on a sample spread over the window sizes (one rank only)."""
+    from paper_2404_04507_gb300 import shard
     eps, phases, cut, kl = W.sweep_params(count, seed=4)
+    mine = (shard.shard((2.0 * kl) ** 4, ws, rank) if ws > 1 else list(range(count)))
     plans = []
-    for i in range(count):
+    for i in mine:
         pb = W.sweep_problem(eps[i], phases[i], int(kl[i]))
         p = iwf.Plan(pb.P, pb.K, pb.L, device=local)
         p.set_potential(pb.modes, pb.coef)
