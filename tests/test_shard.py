@@ -84,3 +84,4 @@ def test_two_gloo_ranks_share_the_sweep(tmp_path):
         assert got[1] == shard.loads(costs, parts).max()
         union = got[2:].astype(int)
         assert sorted(union.tolist()) == list(range(256))       # disjoint and complete
+
